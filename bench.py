@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of one VQE iteration -- QSU, EVC and the adjoint gradient --
+under the lazy qubit-reordering schedule on one GB300 (arXiv 2410.04252).
+
+Default workload: n = 32 qubits, 2^6 virtual chunks, complex64 (32 GiB per
+state), hardware-efficient ansatz of 6 layers (570 gates, 384 parameters),
+1024 random Pauli strings; eager (ad hoc QR) schedule measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica on its own GPU (the path has no exchange step on one
+GPU); the timed region is bracketed by barriers and the max over ranks is
+taken.  --impl reference times the CPU oracle on a bounded sample of the
+same workload on the host cores, scaled to one full iteration.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VQE iter time (QSU+EVC+adjoint grad), HBM GB/s vs peak; lazy-QR vs eager"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=3)
+    ap.add_argument("--n", type=int, default=0, help="override qubit count (smaller runs)")
+    ap.add_argument("--eager-steps", type=int, default=1)
+    ap.add_argument("--eager-warmup", type=int, default=1)
+    ap.add_argument("--no-eager", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=22, help="oracle sample size (qubits)")
+    ap.add_argument("--tile-bits", type=int, default=0)
+    ap.add_argument("--low-bits", type=int, default=0)
+    ap.add_argument("--evc-low-bits", type=int, default=0)
+    ap.add_argument("--evc-span", type=int, default=-1)
+    return ap.parse_args()
+
+
+def rank_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(f):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "kernels.h", "api.cu", "plan.cpp", "sv_internal.h"):
+        with open(os.path.join(ROOT, "paper_2410_04252_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kind: str, launches_bytes: float):
+    """Per-launch DRAM bytes of `kind` from the committed ncu summary, or None
+    if absent or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kind)
+    if not k:
+        return None
+    return k.get("dram_bytes_per_full_launch")
+
+
+# ----------------------------------------------------------------- oracle --
+
+def oracle_sample(cfg_id: int, n_full: int, n_s: int, nterm_sample: int = 16):
+    """Time the oracle on a bounded sample and scale it to one full VQE
+    iteration of the oracle: E and the parameter-shift / finite-difference
+    gradient (1 + 2 * np evaluations of QSU + EVC), each evaluation scaled
+    by 2^(n_full - n_s) and by nterms / nterm_sample for the EVC."""
+    import numpy as np
+    import oracle
+    from paper_2410_04252_gb300 import workloads as W
+    cfg = W.CONFIGS[cfg_id]
+    circ = W.make_circuit(cfg, n_s)
+    params = W.make_params(cfg_id, circ)
+    ham = W.make_hamiltonian(cfg_id, n_s)
+    sub = W.Hamiltonian(n_s, ham.letters[:nterm_sample], ham.coeffs[:nterm_sample])
+    init = W.make_init(cfg, n_s)
+    t0 = time.perf_counter()
+    psi = oracle.apply_circuit(oracle.basis_state(n_s, init), circ, params)
+    t1 = time.perf_counter()
+    oracle.energy(psi, sub)
+    t2 = time.perf_counter()
+    full_circ = W.make_circuit(cfg, n_full)
+    scale = 2.0 ** (n_full - n_s)
+    t_qsu = (t1 - t0) * scale * full_circ.m / max(circ.m, 1)
+    t_evc = (t2 - t1) * scale * cfg["nterms"] / nterm_sample * (n_full / n_s)
+    evals = 1 + 2 * full_circ.nparams
+    est_ms = (t_qsu + t_evc) * evals * 1e3
+    sample = (f"oracle FP64 QSU of the same ansatz at n={n_s} ({circ.m} gates) + EVC of {nterm_sample} "
+              f"of the {cfg['nterms']} strings, {t2 - t0:.2f} s; scaled by 2^{n_full - n_s}, gate count, "
+              f"string count and {evals} evaluations (energy + parameter-shift gradient)")
+    return est_ms, sample, t2 - t0
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def run_reference(args):
+    rank, local, world = rank_info()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    from paper_2410_04252_gb300 import workloads as W
+    cfg = W.CONFIGS[args.config]
+    n_full = args.n or cfg["n"]
+    n_s = min(args.cpu_n, n_full)
+    for _ in range(args.warmup):
+        oracle_sample(args.config, n_full, min(n_s, 16))
+    vals, wall = [], []
+    for _ in range(args.steps):
+        est, sample, w = oracle_sample(args.config, n_full, n_s)
+        vals.append(est)
+        wall.append(w)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["name"], "n": n_full, "g": cfg["g"], "nterms": cfg["nterms"]},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": omp_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": statistics.median(wall)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, local, world = rank_info()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2410_04252_gb300 import sv
+    from paper_2410_04252_gb300 import workloads as W
+
+    cfg = W.CONFIGS[args.config]
+    n = args.n or cfg["n"]
+    g = cfg["g"]
+    dtype = sv.C64 if cfg["dtype"] == "c64" else sv.C128
+    circ = W.make_circuit(cfg, n)
+    params = W.make_params(args.config, circ)
+    ham = W.make_hamiltonian(args.config, n)
+    paulis, coeffs = sv.hamiltonian_arrays(ham)
+    init = W.make_init(cfg, n)
+    opt = sv.default_options(dtype)
+    if args.tile_bits:
+        opt.tile_bits = args.tile_bits
+    if args.low_bits:
+        opt.low_bits = args.low_bits
+    if args.evc_low_bits:
+        opt.evc_low_bits = args.evc_low_bits
+    if args.evc_span >= 0:
+        opt.evc_span = args.evc_span
+    opt.profile = 1
+    sim = sv.StateVector(n, g, dtype, options=opt)
+    sim.ensure_lambda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def step(schedule):
+        return sim.vqe_step(init, circ, params, paulis=paulis, coeffs=coeffs, schedule=schedule)
+
+    t_setup = time.perf_counter()
+    for _ in range(args.warmup):
+        e, gr, _ = step(sv.LAZY)
+    plan_s = time.perf_counter() - t_setup
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    ev0.record(stream)
+    agg = {k: [0, 0.0, 0.0] for k in sv.KERNEL_KINDS}
+    launches = 0
+    counts = {}
+    for _ in range(args.steps):
+        e, gr, _ = step(sv.LAZY)
+        st = sim.last_stats
+        launches += st.launches
+        for i, k in enumerate(sv.KERNEL_KINDS):
+            agg[k][0] += st.kernels[i]
+            agg[k][1] += st.bytes[i]
+            agg[k][2] += st.ms[i]
+        counts = dict(qsu_tiles=st.qsu_tiles, qsu_qrs=st.qsu_qrs, qsu_passes=st.qsu_passes,
+                      evc_tiles=st.evc_tiles, evc_qrs=st.evc_qrs, evc_passes=st.evc_passes,
+                      hpsi_passes=st.hpsi_passes, adj_passes=st.adj_passes)
+    ev1.record(stream)
+    ev1.synchronize()
+    wall_ms = (time.perf_counter() - w0) * 1e3
+    barrier()
+    clk = clocks.stop()
+    dev_ms = ev0.elapsed_time(ev1)
+    tmax = torch.tensor([dev_ms, wall_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dev_ms, wall_ms = float(tmax[0]), float(tmax[1])
+    ms_per_step = dev_ms / args.steps
+    value = dev_ms / (args.steps * world)
+    e2e_value = wall_ms / (args.steps * world)
+
+    # eager schedule on the same GPU (shorter run)
+    eager = None
+    if not args.no_eager:
+        for _ in range(args.eager_warmup):
+            step(sv.EAGER)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        est = None
+        for _ in range(args.eager_steps):
+            ee, eg, _ = step(sv.EAGER)
+            est = sim.last_stats
+        a1.record(stream)
+        a1.synchronize()
+        eager_ms = a0.elapsed_time(a1) / max(args.eager_steps, 1)
+        eager = {"ms_per_step": eager_ms, "speedup_lazy_over_eager": eager_ms / ms_per_step,
+                 "qsu_qrs": est.qsu_qrs, "evc_qrs": est.evc_qrs, "qsu_passes": est.qsu_passes,
+                 "evc_passes": est.evc_passes, "steps": args.eager_steps, "warmup": args.eager_warmup,
+                 "energy_diff_vs_lazy": abs(ee - e), "grad_maxdiff_vs_lazy": float(np.max(np.abs(eg - gr)))}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_src = measured_peaks()
+    kinds = {}
+    for k, (cnt, byts, ms) in agg.items():
+        if cnt:
+            kinds[k] = {"launches_per_step": cnt / args.steps, "ms_per_step": ms / args.steps,
+                        "share": ms / max(sum(v[2] for v in agg.values()), 1e-9),
+                        "algorithmic_GBps": (byts / (ms * 1e-3) / 1e9) if ms > 0 and byts > 0 else None,
+                        "bytes_per_launch": byts / cnt}
+    dom = max((k for k in kinds if agg[k][1] > 0), key=lambda k: agg[k][2])
+    cnt, byts, ms = agg[dom]
+    achieved = byts / (ms * 1e-3) / 1e9
+    traffic = ncu_traffic(dom, byts / cnt)
+    h2d = 2 * params.nbytes
+    d2h = 16 + gr.nbytes
+
+    cpu = None
+    if not args.no_cpu:
+        est_ms, sample, _ = oracle_sample(args.config, n, min(args.cpu_n, n))
+        cpu = {"value": est_ms, "unit": "ms", "cores": omp_threads(), "kind": "oracle", "sample": sample}
+
+    state_gb = (1 << n) * (8 if dtype == sv.C64 else 16) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (f32 math, f64 accumulation)" if dtype == sv.C64 else "c128 (f64)",
+        "data": "synthetic",
+        "config": {"workload": cfg["name"], "n": n, "g": g, "layers": cfg["layers"], "gates": circ.m,
+                   "params": circ.nparams, "nterms": len(coeffs), "schedule": "lazy",
+                   "state_GB": state_gb, "l2": "inputs larger than L2 (state %.1f GB)" % state_gb,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "tile_bits": opt.tile_bits, "low_bits": opt.low_bits, "evc_low_bits": opt.evc_low_bits,
+                   "evc_span": opt.evc_span},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "how": "wall clock around the public vqe_step call (host params/Hamiltonian in, energy+grad out)"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernels": kinds,
+        "counts": counts,
+        "eager": eager,
+        "energy": e,
+        "plan_and_warmup_s": plan_s,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

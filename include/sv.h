@@ -1,0 +1,275 @@
+/*
+ * libsv -- lazy qubit reordering state-vector simulation on one GB300 GPU.
+ *
+ * C ABI of the library.  Plain pointers and sizes only; every entry point
+ * returns an sv_status and never throws.  On failure sv_last_error() gives a
+ * thread-local message.  A handle is used by one host thread at a time.
+ *
+ * Model (arXiv 2410.04252, Sec. III-B):
+ *   The state |psi> of n qubits is 2^n complex amplitudes held in ONE device
+ *   buffer, interleaved (re, im) -- complex64 (float2) or complex128
+ *   (double2), the memory layout of torch.complex64 / torch.complex128.
+ *   Logical qubit q sits at physical index bit l2p[q]; the top g physical bits
+ *   are "global" and split the buffer into 2^g virtual chunks (Eq. sub_sv),
+ *   the low n_L = n - g bits are "local".  Gates and Pauli strings only ever
+ *   touch local physical bits (narrow access, Sec. III-B-3); a qubit
+ *   reordering (QR, Sec. III-B-4) swaps local and global bit pairs in place.
+ *
+ * Conventions for gates (the paper does not define GateFabric's gates):
+ *   U = exp(-i theta G / 2) with G = Y (RY), Z (RZ), Y on span{|10>,|01>} of
+ *   (q0,q1) (GIVENS), Y on span{|q0=q1=1,q2=q3=0>, |q2=q3=1,q0=q1=0>} (DEXC);
+ *   CZ = diag(1,1,1,-1); MATk: caller matrix, row-major complex, target t
+ *   <-> bit t of the matrix index.
+ */
+#ifndef LIBSV_SV_H
+#define LIBSV_SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SV_OK = 0,
+    SV_EINVAL = 1,    /* invalid argument (sizes, qubit indices, NaN, ...) */
+    SV_ENOMEM = 2,    /* device or host allocation failed */
+    SV_ECUDA = 3,     /* a CUDA runtime call or launch failed */
+    SV_EPLAN = 4,     /* internal plan validation failed */
+    SV_ETIMEOUT = 5,  /* a bounded device wait expired */
+    SV_EDEVICE = 6,   /* a kernel reported an error through its status word */
+    SV_ESTATE = 7     /* call not valid in the handle's current state */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* Schedules: EAGER = the ad hoc rule (depth order; before each wide operation
+ * a QR for that operation alone, Sec. V-B-1); LAZY = time-space tiling
+ * (Alg. 1-3 for QSU, Alg. 6 with diagonalization for EVC). */
+typedef enum { SV_SCHED_EAGER = 0, SV_SCHED_LAZY = 1 } sv_schedule;
+
+enum { SV_RY = 0, SV_RZ = 1, SV_CZ = 2, SV_GIVENS = 3, SV_DEXC = 4,
+       SV_MAT1 = 5, SV_MAT2 = 6, SV_MAT4 = 7 };
+
+/* One operator of the QCT form (Sec. III): kind, target qubits q[0..nq-1]
+ * (unused entries -1), parameter index into params[] (-1: none) and, for
+ * MATk, the offset in complex elements of its matrix inside mats[]. */
+typedef struct {
+    int32_t kind;
+    int32_t q[4];
+    int32_t param;
+    int32_t mat;
+} sv_gate;
+
+/* A Pauli string P = i^{|x&z|} X^x Z^z on logical qubits (Eq. pauli_form):
+ * bit q of x is set where P has X or Y, bit q of z where it has Z or Y. */
+typedef struct {
+    uint64_t x;
+    uint64_t z;
+} sv_pauli;
+
+/* Tunables; zero fields take defaults.  sv_options_default() fills them. */
+typedef struct {
+    int32_t tile_bits;          /* k: a gate pass stages 2^k amplitudes (default 13 c64, 12 c128) */
+    int32_t low_bits;           /* contiguous low bits kept in every gate pass (default 4) */
+    int32_t evc_low_bits;       /* contiguous run bits of an EVC / H|psi> coset tile (default 7 c64, 6 c128) */
+    int32_t evc_span;           /* max coset dimension m of an EVC / H|psi> pass (default 6) */
+    int32_t pad_highest;        /* Alg. 3 padding: 1 highest free qubit (default), 0 lowest (printed text) */
+    int32_t checkpoint_every;   /* sv_grad: keep a forward copy every c gate passes, 0 = none */
+    int32_t threads;            /* CTA size for gate passes (default 256) */
+    int32_t blocks_per_sm;      /* persistent grid multiplier (0 = occupancy) */
+    int64_t wait_limit;         /* spin iterations before a device wait gives up (batched kernel) */
+    int32_t profile;            /* 1: time every launch with CUDA events on the stream (sv_stats.ms);
+                                   calls then synchronise before returning */
+    int32_t reserved;
+} sv_options;
+
+/* Kernel kinds counted in sv_stats. */
+enum { SV_K_GATE = 0,   /* fused gate pass */
+       SV_K_QR = 1,     /* qubit reordering (bit-pair swap) */
+       SV_K_EVC = 2,    /* Pauli-string expectation pass */
+       SV_K_HPSI = 3,   /* lambda = H psi pass */
+       SV_K_ADJ = 4,    /* adjoint reverse pass */
+       SV_K_PERM = 5,   /* layout restore (bit-pair swaps) */
+       SV_K_AUX = 6,    /* coefficient prep, reductions, basis reset */
+       SV_K_COUNT = 7 };
+
+/* Counters of one call (optional output). */
+typedef struct {
+    int32_t qsu_tiles, qsu_qrs, qsu_passes;
+    int32_t evc_tiles, evc_qrs, evc_passes;
+    int32_t hpsi_passes, adj_passes;
+    int32_t launches;              /* kernels launched by this call */
+    int32_t plan_cache_hit;        /* every plan came from the cache */
+    double plan_ms;                /* host planning time (0 on a cache hit) */
+    int32_t kernels[SV_K_COUNT];   /* launches per kind */
+    int32_t pad;
+    double bytes[SV_K_COUNT];      /* algorithmic bytes per kind: 2S per gate pass,
+                                      2(1-2^-s)S per QR of s pairs, S per EVC pass,
+                                      2S / 3S per first / later lambda pass, 4S per
+                                      adjoint pass (S = 2^n * amplitude size) */
+    double ms[SV_K_COUNT];         /* device time per kind (options.profile = 1) */
+} sv_stats;
+
+typedef struct sv_handle sv_handle;
+
+void sv_options_default(sv_dtype dt, sv_options *out);
+
+/* Create a simulator for n qubits (1 <= n <= 40) with 2^g virtual chunks
+ * (0 <= g <= n - 4 so that a 4-qubit operator fits the local qubits).
+ * Selects the current CUDA device; allocates nothing on the device until a
+ * buffer is needed.  *out is owned by the caller and freed by sv_destroy. */
+sv_status sv_create(int n, int g, sv_dtype dt, sv_handle **out);
+void sv_destroy(sv_handle *h);
+
+/* Attach a caller-owned device buffer of 2^n amplitudes as the state (e.g. a
+ * torch tensor's data_ptr).  The library never frees it.  bytes must be
+ * >= 2^n * sizeof(amplitude); the pointer must be 256-byte aligned. */
+sv_status sv_attach_state(sv_handle *h, void *dev_ptr, size_t bytes);
+/* Attach a caller-owned device buffer for the adjoint vector lambda = H psi
+ * (same size and alignment rules).  Without it sv_grad allocates one. */
+sv_status sv_attach_lambda(sv_handle *h, void *dev_ptr, size_t bytes);
+
+/* All work is enqueued on this stream (cudaStream_t passed as void*; NULL =
+ * the legacy default stream). */
+sv_status sv_set_stream(sv_handle *h, void *stream);
+sv_status sv_set_options(sv_handle *h, const sv_options *opt);
+sv_status sv_get_options(const sv_handle *h, sv_options *opt);
+
+/* |psi> = |logical_index>, identity layout (l2p[q] = q). Asynchronous. */
+sv_status sv_reset_basis(sv_handle *h, uint64_t logical_index);
+/* Copy 2^n amplitudes in LOGICAL order from src (host or device) into the
+ * state and reset the layout to identity.  Synchronous for host src. */
+sv_status sv_set_state(sv_handle *h, const void *src, int src_is_device);
+/* Copy the state to dst (host or device, 2^n amplitudes).  logical_order=1
+ * undoes the current layout (index bit q = logical qubit q); 0 copies the
+ * physical buffer as is.  Synchronises the stream. */
+sv_status sv_get_state(sv_handle *h, void *dst, int dst_is_device, int logical_order);
+/* l2p[q] = physical bit of logical qubit q (n entries). */
+sv_status sv_get_permutation(const sv_handle *h, int32_t *l2p);
+
+/*
+ * QSU (Eq. vqe_qsu): |psi> <- U_{m-1} ... U_0 |psi> under the given schedule,
+ * starting from the current layout.  LAZY runs the flat time-space tiling of
+ * Alg. 1 (tiles from Alg. 2, remapping by Alg. 3), EAGER the ad hoc rule;
+ * both then group each tile's gates into shared-memory passes of 2^k
+ * amplitudes.  params[np] (host, radians), mats (host, complex interleaved,
+ * nmats complex elements, may be NULL).  The plan is cached on the handle
+ * (Sec. V-C: computed once, reused every VQE iteration).  Asynchronous.
+ * Errors: EINVAL for a qubit >= n, duplicate targets, a parameter index
+ * >= np, a matrix out of range, a NaN parameter.
+ */
+sv_status sv_apply_circuit(sv_handle *h, const sv_gate *gates, size_t m,
+                           const double *params, size_t np,
+                           const double *mats, size_t nmats,
+                           sv_schedule sched, sv_stats *stats);
+
+/* Flags for sv_expect / sv_grad. */
+#define SV_KEEP_LAYOUT 1u    /* sv_expect: restore the entry layout afterwards */
+#define SV_FORWARD_DONE 2u   /* sv_grad: the state already is U|psi0> from the
+                                last sv_apply_circuit of the same circuit, in
+                                that call's final layout */
+
+/*
+ * EVC (Eqs. evc, parallel_evc, par_exp): energy = sum_t coeffs[t] <psi|P_t|psi>.
+ * LAZY: Alg. 6 tiling over X/Y supports (diagonalization: Z on global qubits
+ * becomes a per-chunk sign), QR between tiles; EAGER: strings in index order
+ * with ad hoc QRs.  Inside a tile, strings sharing an X/Y mask share one read
+ * and masks are packed into coset passes.  per_term (nullable) receives
+ * nterms real values <P_t>.  Partial sums are accumulated in FP64 and reduced
+ * in a fixed order.  Synchronises.  Errors: EINVAL for masks >= 2^n, NaN
+ * coefficients, or (LAZY/EAGER alike) a string with more than n - g X/Y
+ * positions, which no virtual-chunk layout can make narrow.
+ */
+sv_status sv_expect(sv_handle *h, const sv_pauli *paulis, const double *coeffs,
+                    size_t nterms, sv_schedule sched, uint32_t flags,
+                    double *energy, double *per_term, sv_stats *stats);
+
+/*
+ * lambda = H|psi> into the handle's lambda buffer (physical layout of psi)
+ * and energy = Re<psi|lambda>.  Used by sv_grad; exposed for testing.
+ * dst (nullable, device) additionally receives a copy of lambda.  Synchronises.
+ */
+sv_status sv_apply_hamiltonian(sv_handle *h, const sv_pauli *paulis, const double *coeffs,
+                               size_t nterms, void *dst_device, double *energy,
+                               sv_stats *stats);
+
+/*
+ * Adjoint gradient of E(theta) = <psi0|U^dagger H U|psi0> (Eqs. vqe,
+ * vqe_qsu, vqe_evc): forward QSU (skipped with SV_FORWARD_DONE), lambda =
+ * H|psi>, then a reverse sweep over the same plan: per gate k in reverse,
+ * grad[param_k] += Im<lambda|G_k|psi> then psi <- U_k^dagger psi and
+ * lambda <- U_k^dagger lambda, with the inverse QRs between tiles.  On
+ * return the state is back at |psi0> (up to rounding) in its entry layout.
+ * grad (host) has np entries.  Synchronises.
+ */
+sv_status sv_grad(sv_handle *h, const sv_gate *gates, size_t m,
+                  const double *params, size_t np, const double *mats, size_t nmats,
+                  const sv_pauli *paulis, const double *coeffs, size_t nterms,
+                  sv_schedule sched, uint32_t flags,
+                  double *energy, double *grad, sv_stats *stats);
+
+/*
+ * One VQE iteration: |psi> = |init>, QSU, EVC (per_term nullable), then the
+ * adjoint gradient of the same energy.  energy comes from the EVC; grad has
+ * np entries.  Synchronises.
+ */
+sv_status sv_vqe_step(sv_handle *h, uint64_t init_index,
+                      const sv_gate *gates, size_t m, const double *params, size_t np,
+                      const double *mats, size_t nmats,
+                      const sv_pauli *paulis, const double *coeffs, size_t nterms,
+                      sv_schedule sched, double *energy, double *per_term, double *grad,
+                      sv_stats *stats);
+
+/*
+ * Host-only planning (no GPU needed), for inspection and bit-exact checks.
+ * sv_plan_qsu: the tile schedule of Alg. 1 (LAZY) or the ad hoc rule (EAGER).
+ * sv_plan_evc: Alg. 6 with diagonalization (LAZY) or index order (EAGER).
+ * l2p_init (nullable) is the starting layout (identity if NULL).
+ */
+typedef struct sv_plan sv_plan;
+sv_status sv_plan_qsu(int n, int g, const sv_gate *gates, size_t m, sv_schedule sched,
+                      const sv_options *opt, const int32_t *l2p_init, sv_plan **out);
+sv_status sv_plan_evc(int n, int g, const sv_pauli *paulis, size_t nterms, sv_schedule sched,
+                      const sv_options *opt, const int32_t *l2p_init, sv_plan **out);
+/* ntiles, total operations scheduled, device passes. */
+sv_status sv_plan_info(const sv_plan *p, int32_t *ntiles, int32_t *nops, int32_t *npasses);
+/* Schedule g: operation indices in execution order at tile granularity (nops). */
+sv_status sv_plan_order(const sv_plan *p, int32_t *order);
+/* Tile t: [begin, end) into the order, local set as a logical bit mask, the
+ * QR performed before it (npairs pairs (local phys, global phys) into
+ * pairs[2*i], pairs[2*i+1], room for 64 pairs) and the layout in force during
+ * it (l2p[n]). */
+sv_status sv_plan_tile(const sv_plan *p, int32_t t, int32_t *begin, int32_t *end,
+                       uint64_t *local_mask, int32_t *npairs, int32_t *pairs, int32_t *l2p);
+/* Pass i of a QSU plan: tile index, staged physical bit mask, and the
+ * operation indices it applies, in order (ops may be NULL to query nops). */
+sv_status sv_plan_pass(const sv_plan *p, int32_t i, int32_t *tile, uint64_t *bits,
+                       int32_t *nops, int32_t *ops);
+void sv_plan_free(sv_plan *p);
+
+/*
+ * Batched VQE (many small independent states, one persistent launch):
+ * state b runs circuit gates[gate_off[b] .. gate_off[b+1]) with parameters
+ * params[param_off[b] ..] from |init_index>, then EVC of the shared
+ * Hamiltonian and the adjoint gradient, all inside ONE kernel launch whose
+ * CTA clusters each own one state at a time.  energies[batch], grads
+ * (param_off[batch] entries, laid out like params) and per-state device
+ * completion times in ns since launch (times_ns, nullable) are written to
+ * host memory.  n <= 20, no virtual chunks.  Synchronises.
+ */
+sv_status sv_batch_run(int n, sv_dtype dt, int batch,
+                       const sv_gate *gates, const int32_t *gate_off,
+                       const double *params, const int32_t *param_off,
+                       const sv_pauli *paulis, const double *coeffs, size_t nterms,
+                       uint64_t init_index, const sv_options *opt, void *stream,
+                       double *energies, double *grads, double *times_ns, sv_stats *stats);
+
+const char *sv_last_error(void);
+const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -173,7 +173,7 @@ def flat_tiling(n: int, T: list[tuple], nL: int, pad: str = "highest", l2p=None)
     Q = set(range(n))
     l2p = list(range(n)) if l2p is None else list(l2p)
     cur = {q for q in range(n) if l2p[q] < nL}
-    QL = set(range(nL))
+    QL = set(cur)          # {0..n_L-1} for the identity layout (Alg. 1, line 2)
     remain = depth_sort(T)
     while remain:
         G = tile_construction(QL, remain, T)

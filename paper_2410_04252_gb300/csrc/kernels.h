@@ -1,0 +1,74 @@
+// Launchers of the device kernels (kernels.cu).  All take a stream and return
+// the CUDA error of the launch.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sv_internal.h"
+
+namespace sv {
+
+// Gate / adjoint pass: 2^k staged amplitudes; tile bits 0..nlow-1 are
+// physical bits 0..nlow-1, tile bits nlow..k-1 are hi[]; out[] lists the
+// physical bits that are not staged (they index the tiles).
+struct GatePassArgs {
+    int n, k, nlow, nhi, nout, op_begin, op_end;
+    int8_t hi[40];
+    int8_t out[64];
+};
+
+// Coset pass (EVC / H|psi>): 2^(kl+m) staged amplitudes, runs of 2^kl
+// contiguous ones at rep ^ span(a); free[] lists the bits >= kl that are not
+// pivots (they index the coset representatives).
+struct CosetArgs {
+    int n, kl, m, nfree, g_begin, g_end, s_begin, s_end;
+    uint64_t basis[kMaxSpan];
+    int8_t freeb[64];
+};
+
+struct DevGroup {
+    uint64_t x;
+    uint32_t X;
+    int32_t s_begin, s_end;
+    int32_t pad;
+};
+struct DevString {
+    uint64_t z;
+    double coef;
+    int32_t nY;
+    int32_t pad;
+};
+
+int device_sms();
+int gate_pass_grid(sv_dtype dt, int k, int nlow, int nops, int threads, int blocks_per_sm);
+int adj_pass_grid(sv_dtype dt, int k, int nlow, int nops, int threads, int blocks_per_sm);
+int coset_grid(sv_dtype dt, int E, int blocks_per_sm, bool hpsi);
+
+cudaError_t launch_prep(sv_dtype dt, cudaStream_t st, const int32_t *gparam, const double *params,
+                        int m, void *coef);
+cudaError_t launch_set_basis(sv_dtype dt, cudaStream_t st, void *psi, size_t bytes, uint64_t index);
+cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi,
+                             const GatePassArgs &a, const DevOp *ops, const void *coef, const void *mats);
+cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi, void *lam,
+                            const GatePassArgs &a, const DevOp *ops, const void *coef, const void *mats,
+                            double *part, int part_stride);
+// In-place swap of disjoint physical bit pairs (pairs[2i], pairs[2i+1]).
+cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const int32_t *pairs,
+                           int npairs, int blocks_per_sm);
+cudaError_t launch_evc_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, const CosetArgs &a,
+                            const DevGroup *groups, const DevString *strs, double *part, int part_stride);
+cudaError_t launch_hpsi_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, void *lam,
+                             const CosetArgs &a, const DevGroup *groups, const DevString *strs,
+                             int first, int last, double *epart);
+// out[s] = sum over b < nblocks of part[b * stride + s], s in [s_begin, s_end); fixed order.
+cudaError_t launch_reduce_rows(cudaStream_t st, const double *part, int nblocks, int stride,
+                               int s_begin, int s_end, double *out);
+// grad[param[i]] accumulation in a fixed order: grad[p] = sum_{i in list(p)} opval[i].
+cudaError_t launch_scatter(cudaStream_t st, const double *opval, const int32_t *csr_off,
+                           const int32_t *csr_idx, int np, double *grad);
+// energy = sum_t coef_t * slotval[slot_t] and per-term values.
+cudaError_t launch_energy(cudaStream_t st, const double *slotval, const int32_t *term_slot,
+                          const double *coeffs, int nterms, double *per_term, double *energy);
+cudaError_t launch_copy(sv_dtype dt, cudaStream_t st, void *dst, const void *src, size_t n_elems);
+
+}  // namespace sv

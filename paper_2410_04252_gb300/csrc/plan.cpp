@@ -1,0 +1,784 @@
+// Host planner: the paper's schedules (Alg. 1-3, the ad hoc rule, Alg. 6 with
+// diagonalization), the QR pairing, and this library's pass planning (gate
+// passes inside a tile, coset passes for Pauli strings).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace {
+
+inline int popc(uint64_t v) { return __builtin_popcountll(v); }
+inline int hibit(uint64_t v) { return 63 - __builtin_clzll(v); }
+inline int lobit(uint64_t v) { return __builtin_ctzll(v); }
+inline uint64_t bit(int q) { return 1ull << q; }
+
+int gate_nq(int kind) {
+    switch (kind) {
+    case SV_RY: case SV_RZ: case SV_MAT1: return 1;
+    case SV_CZ: case SV_GIVENS: case SV_MAT2: return 2;
+    case SV_DEXC: case SV_MAT4: return 4;
+    default: return -1;
+    }
+}
+
+uint64_t local_set(const std::vector<int32_t> &l2p, int nL) {
+    uint64_t m = 0;
+    for (size_t q = 0; q < l2p.size(); ++q)
+        if (l2p[q] < nL) m |= bit((int)q);
+    return m;
+}
+
+uint64_t to_physical(uint64_t logical, const std::vector<int32_t> &l2p) {
+    uint64_t out = 0;
+    while (logical) {
+        int q = lobit(logical);
+        logical &= logical - 1;
+        out |= bit(l2p[q]);
+    }
+    return out;
+}
+
+// depth(U) = 0 if no earlier operator shares a qubit, else 1 + the largest
+// depth among earlier operators sharing a qubit (critical path, Sec. III-A).
+std::vector<int32_t> depths(const std::vector<Op> &ops) {
+    int32_t last[64];
+    std::fill(last, last + 64, -1);
+    std::vector<int32_t> d(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        int32_t di = 0;
+        for (int t = 0; t < ops[i].nq; ++t)
+            if (last[ops[i].q[t]] >= 0) di = std::max(di, last[ops[i].q[t]] + 1);
+        for (int t = 0; t < ops[i].nq; ++t) last[ops[i].q[t]] = di;
+        d[i] = di;
+    }
+    return d;
+}
+
+// Ascending depth; ties by the sorted target tuple, then input position
+// (Sec. IV-A-1).  The sort is stable, so equal keys keep input order.
+std::vector<int32_t> depth_sort(const std::vector<Op> &ops) {
+    std::vector<int32_t> d = depths(ops);
+    std::vector<std::vector<int32_t>> key(ops.size());
+    for (size_t i = 0; i < ops.size(); ++i) {
+        key[i].assign(ops[i].q, ops[i].q + ops[i].nq);
+        std::sort(key[i].begin(), key[i].end());
+    }
+    std::vector<int32_t> idx(ops.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        if (d[a] != d[b]) return d[a] < d[b];
+        return key[a] < key[b];
+    });
+    return idx;
+}
+
+// Alg. 2 (P1): single scan in depth order.
+void tile_construction(uint64_t QL, const std::vector<int32_t> &remain, const std::vector<Op> &ops,
+                       std::vector<int32_t> &G) {
+    uint64_t avail = QL;
+    G.clear();
+    for (int32_t u : remain) {
+        uint64_t t = ops[u].tmask;
+        if ((t & ~avail) == 0) G.push_back(u);
+        else avail &= ~t;
+        if (!avail) break;
+    }
+}
+
+// Alg. 3 (P2), with the padding rule selectable.
+uint64_t qubit_mapping(uint64_t Q, const std::vector<int32_t> &remain, const std::vector<Op> &ops,
+                       int nL, bool pad_highest) {
+    uint64_t avail = Q, QL = 0;
+    for (int32_t u : remain) {
+        uint64_t t = ops[u].tmask;
+        if ((t & ~avail) == 0 && popc(QL | t) <= nL) QL |= t;
+        else avail &= ~t;
+        if (!avail) break;
+    }
+    if (!QL) return 0;
+    uint64_t fr = Q & ~QL;
+    while (popc(QL) < nL && fr) {
+        int q = pad_highest ? hibit(fr) : lobit(fr);
+        QL |= bit(q);
+        fr &= ~bit(q);
+    }
+    return QL;
+}
+
+// Physical pairs of one QR: outgoing locals and incoming globals, each sorted
+// by current physical position, swapped pairwise.  Updates l2p.
+void qr_pairs(std::vector<int32_t> &l2p, uint64_t old_loc, uint64_t new_loc, std::vector<int32_t> &pairs) {
+    std::vector<int32_t> out, in;
+    for (uint64_t v = old_loc & ~new_loc; v; v &= v - 1) out.push_back(lobit(v));
+    for (uint64_t v = new_loc & ~old_loc; v; v &= v - 1) in.push_back(lobit(v));
+    auto bypos = [&](int32_t a, int32_t b) { return l2p[a] < l2p[b]; };
+    std::sort(out.begin(), out.end(), bypos);
+    std::sort(in.begin(), in.end(), bypos);
+    pairs.clear();
+    for (size_t i = 0; i < out.size() && i < in.size(); ++i) {
+        int32_t pa = l2p[out[i]], pb = l2p[in[i]];
+        pairs.push_back(pa);
+        pairs.push_back(pb);
+        l2p[out[i]] = pb;
+        l2p[in[i]] = pa;
+    }
+}
+
+std::string flat_tiling(int n, int nL, const std::vector<Op> &ops, bool pad_highest,
+                        std::vector<int32_t> l2p, std::vector<int32_t> &order, std::vector<Tile> &tiles,
+                        std::vector<int32_t> &final_l2p) {
+    const uint64_t Q = (n == 64) ? ~0ull : (bit(n) - 1);
+    uint64_t cur = local_set(l2p, nL);
+    uint64_t QL = cur;
+    std::vector<int32_t> remain = depth_sort(ops), G, next;
+    std::vector<char> taken(ops.size(), 0);
+    int stall = 0;
+    while (!remain.empty()) {
+        tile_construction(QL, remain, ops, G);
+        if (!G.empty()) {
+            Tile t;
+            t.begin = (int32_t)order.size();
+            order.insert(order.end(), G.begin(), G.end());
+            t.end = (int32_t)order.size();
+            t.local_mask = QL;
+            if (QL != cur) qr_pairs(l2p, cur, QL, t.pairs);
+            t.l2p = l2p;
+            cur = QL;
+            tiles.push_back(std::move(t));
+            for (int32_t u : G) taken[u] = 1;
+            next.clear();
+            for (int32_t u : remain)
+                if (!taken[u]) next.push_back(u);
+            remain.swap(next);
+            stall = 0;
+        } else if (++stall > 1) {
+            return "flat tiling made no progress";
+        }
+        if (remain.empty()) break;
+        QL = qubit_mapping(Q, remain, ops, nL, pad_highest);
+        if (!QL) return "qubit mapping returned an empty set";
+    }
+    final_l2p = l2p;
+    return "";
+}
+
+// The ad hoc rule: depth (or given) order; before an operation with a global
+// target, evict as many locals outside its targets as it has global targets,
+// least recently used first (never used = -1), ties to the highest index.
+std::string adhoc_schedule(int n, int nL, const std::vector<Op> &ops, const std::vector<int32_t> &seq,
+                           std::vector<int32_t> l2p, std::vector<int32_t> &order,
+                           std::vector<Tile> &tiles, std::vector<int32_t> &final_l2p) {
+    uint64_t QL = local_set(l2p, nL);
+    std::vector<int64_t> last(n, -1);
+    Tile cur;
+    cur.begin = (int32_t)order.size();
+    cur.local_mask = QL;
+    cur.l2p = l2p;
+    for (size_t x = 0; x < seq.size(); ++x) {
+        int32_t u = seq[x];
+        uint64_t t = ops[u].tmask;
+        if (t & ~QL) {
+            uint64_t inn = t & ~QL;
+            int k = popc(inn);
+            std::vector<int32_t> cand;
+            for (uint64_t v = QL & ~t; v; v &= v - 1) cand.push_back(lobit(v));
+            std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+                if (last[a] != last[b]) return last[a] < last[b];
+                return a > b;
+            });
+            if ((int)cand.size() < k) return "operation wider than the local qubits";
+            uint64_t evict = 0;
+            for (int i = 0; i < k; ++i) evict |= bit(cand[i]);
+            uint64_t newQL = (QL & ~evict) | inn;
+            if ((int32_t)order.size() > cur.begin) {
+                cur.end = (int32_t)order.size();
+                tiles.push_back(cur);
+            }
+            cur = Tile();
+            cur.begin = (int32_t)order.size();
+            qr_pairs(l2p, QL, newQL, cur.pairs);
+            QL = newQL;
+            cur.local_mask = QL;
+            cur.l2p = l2p;
+        }
+        order.push_back(u);
+        for (int i = 0; i < ops[u].nq; ++i) last[ops[u].q[i]] = (int64_t)x;
+    }
+    if ((int32_t)order.size() > cur.begin) {
+        cur.end = (int32_t)order.size();
+        tiles.push_back(cur);
+    }
+    final_l2p = l2p;
+    return "";
+}
+
+// ------------------------------------------------------------ gate passes --
+// Inside a tile every gate is narrow.  Gates are grouped into passes that each
+// stage 2^k amplitudes in shared memory: the staged physical set always holds
+// the `low` lowest bits (coalesced runs) and is chosen like Alg. 3 (targets of
+// the earliest remaining gates), padded with the lowest free local bits; the
+// pass then takes gates like Alg. 2 (a gate that does not fit blocks its
+// targets), which keeps the dependency order C1.
+void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low) {
+    const int nL = P.nL;
+    k = std::min(k, nL);
+    low = std::min(low, k);
+    const uint64_t localbits = (nL == 64) ? ~0ull : (bit(nL) - 1);
+    const uint64_t lowmask = bit(low) - 1;
+    for (size_t ti = 0; ti < P.tiles.size(); ++ti) {
+        const Tile &T = P.tiles[ti];
+        std::vector<int32_t> remain(P.order.begin() + T.begin, P.order.begin() + T.end);
+        std::vector<uint64_t> pm(ops.size(), 0);
+        for (int32_t u : remain) pm[u] = to_physical(ops[u].tmask, T.l2p);
+        std::vector<int32_t> G, next;
+        while (!remain.empty()) {
+            uint64_t S = lowmask, avail = localbits;
+            for (int32_t u : remain) {
+                uint64_t t = pm[u];
+                if ((t & ~avail) == 0 && popc(S | t) <= k) S |= t;
+                else avail &= ~t;
+                if (!avail || popc(S) == k) break;
+            }
+            for (uint64_t fr = localbits & ~S; popc(S) < k && fr; fr &= fr - 1) S |= bit(lobit(fr));
+            uint64_t av = S;
+            G.clear();
+            for (int32_t u : remain) {
+                uint64_t t = pm[u];
+                if ((t & ~av) == 0) G.push_back(u);
+                else av &= ~t;
+                if (!av || (int)G.size() >= kMaxPassOps) break;
+            }
+            GatePass gp;
+            gp.tile = (int32_t)ti;
+            gp.k = popc(S);
+            int nl = 0;
+            while (nl < 64 && (S >> nl & 1)) ++nl;
+            gp.nlow = nl;
+            gp.bits = S;
+            gp.op_begin = (int32_t)P.ops.size();
+            // tile-local position of each staged physical bit
+            int8_t loc[64];
+            int c = 0;
+            for (int b = 0; b < 64; ++b)
+                if (S >> b & 1) loc[b] = (int8_t)c++;
+            for (int32_t u : G) {
+                DevOp d;
+                d.kind = ops[u].kind;
+                for (int i = 0; i < 4; ++i)
+                    d.t[i] = (int8_t)(i < ops[u].nq ? loc[T.l2p[ops[u].q[i]]] : -1);
+                d.gate = u;
+                d.mat = ops[u].mat;
+                P.ops.push_back(d);
+            }
+            gp.op_end = (int32_t)P.ops.size();
+            P.passes.push_back(gp);
+            std::vector<char> in(ops.size(), 0);
+            for (int32_t u : G) in[u] = 1;
+            next.clear();
+            for (int32_t u : remain)
+                if (!in[u]) next.push_back(u);
+            remain.swap(next);
+        }
+    }
+}
+
+// ---------------------------------------------------------- coset passes --
+// Strings sharing a physical X/Y mask x form a group: one read of psi serves
+// all of them.  A pass stages 2^(kl+m) amplitudes: the 2^m runs of 2^kl
+// contiguous amplitudes at R ^ span(a), a in [0, 2^m), for one coset
+// representative R of an m-dimensional span V over bits >= kl.  Every group
+// whose high part x >> kl lies in V pairs amplitudes inside the staged set, so
+// all such groups share the pass.  Two greedy choices of V are tried per pass
+// (V spanned by single bits, V spanned by the most frequent masks); the one
+// covering more strings is kept.
+struct GroupIn {
+    uint64_t x;
+    std::vector<std::pair<uint64_t, double>> zs;   // unique z with summed coefficient
+    std::vector<std::vector<int32_t>> terms;       // input terms per z
+};
+
+void plan_cosets(EvcPlan &P, std::vector<GroupIn> &groups, int kl, int mmax, uint64_t allowed) {
+    const uint64_t lowmask = bit(kl) - 1;
+    std::vector<int32_t> remaining(groups.size());
+    std::iota(remaining.begin(), remaining.end(), 0);
+    while (!remaining.empty()) {
+        // candidate A: bit spans
+        auto run = [&](bool bits_mode, std::vector<uint64_t> &basis, std::vector<int32_t> &pivot,
+                       std::vector<int32_t> &sel) {
+            basis.clear(); pivot.clear(); sel.clear();
+            auto reduce = [&](uint64_t r) {
+                for (size_t j = 0; j < basis.size(); ++j)
+                    if (r >> pivot[j] & 1) r ^= basis[j];
+                return r;
+            };
+            auto insert = [&](uint64_t v) {
+                v = reduce(v);
+                if (!v) return;
+                int p = hibit(v);
+                for (auto &b : basis)
+                    if (b >> p & 1) b ^= v;
+                basis.push_back(v);
+                pivot.push_back(p);
+            };
+            if (bits_mode) {
+                std::vector<int32_t> byw(remaining);
+                std::stable_sort(byw.begin(), byw.end(), [&](int32_t a, int32_t b) {
+                    return popc(groups[a].x & ~lowmask) < popc(groups[b].x & ~lowmask);
+                });
+                uint64_t B = 0;
+                for (int32_t gi : byw) {
+                    uint64_t h = groups[gi].x & ~lowmask & allowed;
+                    if (popc(B | h) <= mmax) B |= h;
+                    if (popc(B) == mmax) break;
+                }
+                for (uint64_t v = B; v; v &= v - 1) insert(bit(lobit(v)));
+            } else {
+                while ((int)basis.size() < mmax) {
+                    std::unordered_map<uint64_t, int64_t> freq;
+                    uint64_t best = 0;
+                    int64_t bestc = 0;
+                    for (int32_t gi : remaining) {
+                        uint64_t r = reduce(groups[gi].x & ~lowmask);
+                        if (!r) continue;
+                        int64_t c = (freq[r] += (int64_t)groups[gi].zs.size());
+                        if (c > bestc) { bestc = c; best = r; }
+                    }
+                    if (!best) break;
+                    insert(best);
+                }
+            }
+            int64_t strings = 0;
+            for (int32_t gi : remaining) {
+                if (reduce(groups[gi].x & ~lowmask)) continue;
+                int64_t c = (int64_t)groups[gi].zs.size();
+                if (strings + c > kMaxPassStrings && !sel.empty()) continue;
+                sel.push_back(gi);
+                strings += c;
+            }
+            return strings;
+        };
+        std::vector<uint64_t> bA, bB;
+        std::vector<int32_t> pA, pB, sA, sB;
+        int64_t cA = run(true, bA, pA, sA);
+        int64_t cB = run(false, bB, pB, sB);
+        bool useA = cA >= cB;
+        std::vector<uint64_t> &basis = useA ? bA : bB;
+        std::vector<int32_t> &pivot = useA ? pA : pB;
+        std::vector<int32_t> &sel = useA ? sA : sB;
+        // pad the span with unit vectors on the lowest free allowed bits >= kl,
+        // so every pass stages the same number of amplitudes (the low ones
+        // extend the contiguous runs); the span only grows
+        uint64_t pivmask = 0;
+        for (int32_t pv : pivot) pivmask |= bit(pv);
+        for (int b = kl; b < 64 && (int)basis.size() < mmax; ++b) {
+            if (!(allowed >> b & 1) || (pivmask >> b & 1)) continue;
+            for (auto &v : basis)
+                if (v >> b & 1) v ^= bit(b);
+            basis.push_back(bit(b));
+            pivot.push_back(b);
+            pivmask |= bit(b);
+        }
+        CosetPass cp;
+        cp.kl = kl;
+        cp.m = (int32_t)basis.size();
+        for (int j = 0; j < cp.m; ++j) { cp.basis[j] = basis[j]; cp.pivot[j] = pivot[j]; }
+        cp.g_begin = (int32_t)P.groups.size();
+        cp.s_begin = (int32_t)P.strings.size();
+        std::vector<char> in(groups.size(), 0);
+        for (int32_t gi : sel) {
+            in[gi] = 1;
+            GroupIn &G = groups[gi];
+            EvcGroup eg;
+            eg.x = G.x;
+            uint32_t c = 0;
+            uint64_t h = G.x & ~lowmask;
+            for (int j = 0; j < cp.m; ++j)
+                if (h >> pivot[j] & 1) c |= 1u << j;
+            eg.X = (c << kl) | (uint32_t)(G.x & lowmask);
+            eg.s_begin = (int32_t)P.strings.size();
+            for (size_t s = 0; s < G.zs.size(); ++s) {
+                EvcString es;
+                es.z = G.zs[s].first;
+                es.nY = popc(G.x & G.zs[s].first) & 3;
+                es.coef = G.zs[s].second;
+                for (int32_t t : G.terms[s]) P.term_slot[t] = (int32_t)P.strings.size();
+                P.strings.push_back(es);
+            }
+            eg.s_end = (int32_t)P.strings.size();
+            P.groups.push_back(eg);
+        }
+        cp.g_end = (int32_t)P.groups.size();
+        cp.s_end = (int32_t)P.strings.size();
+        P.passes.push_back(cp);
+        std::vector<int32_t> next;
+        for (int32_t gi : remaining)
+            if (!in[gi]) next.push_back(gi);
+        remaining.swap(next);
+    }
+}
+
+void group_terms(const std::vector<int32_t> &terms, const sv_pauli *p, const double *coeffs,
+                 const std::vector<int32_t> &l2p, std::vector<GroupIn> &groups) {
+    std::unordered_map<uint64_t, int32_t> gidx;
+    for (int32_t t : terms) {
+        uint64_t x = to_physical(p[t].x, l2p), z = to_physical(p[t].z, l2p);
+        // a group holds at most kMaxGroupStrings distinct z; a full group for
+        // this x is closed and a new one (same x) opened
+        auto it = gidx.find(x);
+        int32_t gi;
+        if (it == gidx.end()) {
+            gi = (int32_t)groups.size();
+            gidx[x] = gi;
+            groups.push_back(GroupIn{x, {}, {}});
+        } else {
+            gi = it->second;
+        }
+        size_t s = 0;
+        while (s < groups[gi].zs.size() && groups[gi].zs[s].first != z) ++s;
+        if (s == groups[gi].zs.size() && s >= (size_t)kMaxGroupStrings) {
+            gi = (int32_t)groups.size();
+            gidx[x] = gi;
+            groups.push_back(GroupIn{x, {}, {}});
+            s = 0;
+        }
+        GroupIn &G = groups[gi];
+        if (s == G.zs.size()) {
+            G.zs.push_back({z, 0.0});
+            G.terms.push_back({});
+        }
+        G.zs[s].second += coeffs ? coeffs[t] : 0.0;
+        G.terms[s].push_back(t);
+    }
+}
+
+// Lexicographic rank of k-combinations of {0..n-1} via binomial sums.
+struct Binom {
+    std::vector<std::vector<int64_t>> C;
+    explicit Binom(int n) : C(n + 2, std::vector<int64_t>(n + 2, 0)) {
+        for (int a = 0; a <= n + 1; ++a) {
+            C[a][0] = 1;
+            for (int b = 1; b <= a; ++b) C[a][b] = C[a - 1][b - 1] + (b <= a - 1 ? C[a - 1][b] : 0);
+        }
+    }
+    int64_t operator()(int a, int b) const {
+        if (a < 0 || b < 0 || b > a) return 0;
+        return C[a][b];
+    }
+};
+
+// Visit every k-subset of `free` (ascending) with its lexicographic rank
+// among the k-subsets of {0..n-1}.
+template <class F>
+void for_each_subset_rank(const std::vector<int> &fr, int k, int n, const Binom &B, F &&f) {
+    if (k == 0) { f(0); return; }
+    std::vector<int> idx(k);
+    std::vector<int64_t> acc(k + 1, 0);
+    // term for position i with value c given previous value pc:
+    //   C(n - pc - 1, k - i) - C(n - c, k - i)
+    int m = (int)fr.size();
+    if (m < k) return;
+    int i = 0;
+    idx[0] = 0;
+    while (true) {
+        if (idx[i] <= m - (k - i)) {
+            int pc = (i == 0) ? -1 : fr[idx[i - 1]];
+            int c = fr[idx[i]];
+            acc[i + 1] = acc[i] + B(n - pc - 1, k - i) - B(n - c, k - i);
+            if (i == k - 1) {
+                f(acc[k]);
+                ++idx[i];
+            } else {
+                idx[i + 1] = idx[i] + 1;
+                ++i;
+            }
+        } else {
+            if (i == 0) break;
+            --i;
+            ++idx[i];
+        }
+    }
+}
+
+// Alg. 6 with diagonalization: targets are X/Y supports; identical supports
+// merged with multiplicity; each step takes the first global set (in
+// lexicographic order) whose complement holds the most remaining strings.
+// Counts are maintained incrementally: a support x adds its multiplicity to
+// every global set disjoint from it.
+std::string tiling_pauli_strings(int n, int nG, const sv_pauli *p, size_t nterms,
+                                 std::vector<std::vector<int32_t>> &tiles_terms,
+                                 std::vector<uint64_t> &tiles_local) {
+    const uint64_t Q = bit(n) - 1;
+    std::unordered_map<uint64_t, int32_t> xi;
+    std::vector<uint64_t> xs;
+    std::vector<std::vector<int32_t>> members;
+    for (size_t t = 0; t < nterms; ++t) {
+        uint64_t x = p[t].x;
+        if (popc(x) > n - nG) return "a Pauli string has more X/Y positions than local qubits";
+        auto it = xi.find(x);
+        if (it == xi.end()) {
+            xi[x] = (int32_t)xs.size();
+            xs.push_back(x);
+            members.push_back({(int32_t)t});
+        } else {
+            members[it->second].push_back((int32_t)t);
+        }
+    }
+    Binom B(n);
+    int64_t ncand = B(n, nG);
+    if (ncand > 60000000) return "Alg. 6 search space C(n, n_G) too large";
+    std::vector<int64_t> count((size_t)ncand, 0);
+    auto add = [&](size_t gi, int64_t w) {
+        std::vector<int> fr;
+        for (uint64_t v = Q & ~xs[gi]; v; v &= v - 1) fr.push_back(lobit(v));
+        for_each_subset_rank(fr, nG, n, B, [&](int64_t r) { count[(size_t)r] += w; });
+    };
+    for (size_t gi = 0; gi < xs.size(); ++gi) add(gi, (int64_t)members[gi].size());
+    std::vector<char> alive(xs.size(), 1);
+    size_t left = xs.size();
+    while (left) {
+        int64_t best = 0, bestr = -1;
+        for (int64_t r = 0; r < ncand; ++r)
+            if (best < count[(size_t)r]) { best = count[(size_t)r]; bestr = r; }
+        if (bestr < 0) return "no mapping holds a remaining Pauli string";
+        // unrank bestr -> global set
+        uint64_t G = 0;
+        {
+            int64_t r = bestr;
+            int c = 0;
+            for (int i = 0; i < nG; ++i) {
+                while (true) {
+                    int64_t cnt = B(n - c - 1, nG - i - 1);
+                    if (r < cnt) break;
+                    r -= cnt;
+                    ++c;
+                }
+                G |= bit(c);
+                ++c;
+            }
+        }
+        std::vector<int32_t> tile;
+        for (size_t gi = 0; gi < xs.size(); ++gi) {
+            if (!alive[gi] || (xs[gi] & G)) continue;
+            alive[gi] = 0;
+            --left;
+            tile.insert(tile.end(), members[gi].begin(), members[gi].end());
+            add(gi, -(int64_t)members[gi].size());
+        }
+        std::sort(tile.begin(), tile.end());
+        tiles_terms.push_back(tile);
+        tiles_local.push_back(Q & ~G);
+    }
+    return "";
+}
+
+}  // namespace
+
+uint64_t hash_bytes(const void *p, size_t n, uint64_t h) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= c[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+std::string validate_gates(int n, const sv_gate *gates, size_t m, size_t np, size_t nmats) {
+    for (size_t i = 0; i < m; ++i) {
+        const sv_gate &g = gates[i];
+        int nq = gate_nq(g.kind);
+        if (nq < 0) return "gate " + std::to_string(i) + ": unknown kind";
+        uint64_t seen = 0;
+        for (int t = 0; t < 4; ++t) {
+            if (t < nq) {
+                if (g.q[t] < 0 || g.q[t] >= n) return "gate " + std::to_string(i) + ": qubit out of range";
+                if (seen & bit(g.q[t])) return "gate " + std::to_string(i) + ": duplicate target";
+                seen |= bit(g.q[t]);
+            }
+        }
+        bool parametric = g.kind == SV_RY || g.kind == SV_RZ || g.kind == SV_GIVENS || g.kind == SV_DEXC;
+        if (parametric && (g.param < 0 || (size_t)g.param >= np))
+            return "gate " + std::to_string(i) + ": parameter index out of range";
+        if (g.kind >= SV_MAT1 && nmats != (size_t)-1) {   // (size_t)-1: planning only, no matrices
+            size_t dim = (size_t)1 << nq;
+            if (g.mat < 0 || (size_t)g.mat + dim * dim > nmats)
+                return "gate " + std::to_string(i) + ": matrix out of range";
+        }
+    }
+    return "";
+}
+
+std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, const PlanOptions &o,
+                     const std::vector<int32_t> &l2p_init, QsuPlan &P) {
+    P = QsuPlan();
+    P.n = n; P.g = g; P.nL = n - g;
+    std::vector<Op> ops(m);
+    for (size_t i = 0; i < m; ++i) {
+        Op &op = ops[i];
+        op.kind = gates[i].kind;
+        op.nq = gate_nq(op.kind);
+        for (int t = 0; t < op.nq; ++t) {
+            op.q[t] = gates[i].q[t];
+            op.tmask |= bit(op.q[t]);
+        }
+        op.param = gates[i].param;
+        op.mat = gates[i].mat;
+        if (op.nq > P.nL) return "an operator is wider than the local qubits";
+    }
+    P.init_l2p = l2p_init;
+    std::string err;
+    if (lazy) {
+        err = flat_tiling(n, P.nL, ops, o.pad_highest, l2p_init, P.order, P.tiles, P.final_l2p);
+    } else {
+        err = adhoc_schedule(n, P.nL, ops, depth_sort(ops), l2p_init, P.order, P.tiles, P.final_l2p);
+    }
+    if (!err.empty()) return err;
+    if (P.tiles.empty()) P.final_l2p = l2p_init;
+    int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
+    plan_gate_passes(P, ops, k, o.low_bits);
+    return "";
+}
+
+std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size_t nterms, bool lazy,
+                     const PlanOptions &o, const std::vector<int32_t> &l2p_init, EvcPlan &P) {
+    P = EvcPlan();
+    P.n = n; P.g = g; P.nL = n - g;
+    P.init_l2p = l2p_init;
+    P.term_slot.assign(nterms, -1);
+    std::vector<int32_t> l2p = l2p_init;
+    uint64_t cur = local_set(l2p, P.nL);
+    std::vector<std::vector<int32_t>> tt;
+    std::vector<uint64_t> tl;
+    if (lazy) {
+        std::string err = tiling_pauli_strings(n, g, p, nterms, tt, tl);
+        if (!err.empty()) return err;
+        for (size_t i = 0; i < tt.size(); ++i) {
+            Tile t;
+            t.begin = (int32_t)P.order.size();
+            P.order.insert(P.order.end(), tt[i].begin(), tt[i].end());
+            t.end = (int32_t)P.order.size();
+            t.local_mask = tl[i];
+            if (tl[i] != cur) qr_pairs(l2p, cur, tl[i], t.pairs);
+            cur = tl[i];
+            t.l2p = l2p;
+            P.tiles.push_back(std::move(t));
+        }
+        P.final_l2p = l2p;
+    } else {
+        // targets: full support when it fits n_L qubits, else the X/Y support
+        std::vector<uint64_t> tms(nterms);
+        for (size_t t = 0; t < nterms; ++t) {
+            uint64_t full = p[t].x | p[t].z;
+            tms[t] = popc(full) <= P.nL ? full : p[t].x;
+            if (popc(tms[t]) > P.nL) return "a Pauli string has more X/Y positions than local qubits";
+        }
+        // the ad hoc rule on masks (a string may have more than 4 targets)
+        uint64_t QL = cur;
+        std::vector<int64_t> last(n, -1);
+        Tile ct;
+        ct.begin = 0;
+        ct.local_mask = QL;
+        ct.l2p = l2p;
+        for (size_t x = 0; x < nterms; ++x) {
+            uint64_t t = tms[x];
+            if (t & ~QL) {
+                uint64_t inn = t & ~QL;
+                int k = popc(inn);
+                std::vector<int32_t> cand;
+                for (uint64_t v = QL & ~t; v; v &= v - 1) cand.push_back(lobit(v));
+                std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) {
+                    if (last[a] != last[b]) return last[a] < last[b];
+                    return a > b;
+                });
+                uint64_t ev = 0;
+                for (int i = 0; i < k; ++i) ev |= bit(cand[i]);
+                uint64_t nQL = (QL & ~ev) | inn;
+                if ((int32_t)P.order.size() > ct.begin) {
+                    ct.end = (int32_t)P.order.size();
+                    P.tiles.push_back(ct);
+                }
+                ct = Tile();
+                ct.begin = (int32_t)P.order.size();
+                qr_pairs(l2p, QL, nQL, ct.pairs);
+                QL = nQL;
+                ct.local_mask = QL;
+                ct.l2p = l2p;
+            }
+            P.order.push_back((int32_t)x);
+            for (uint64_t v = t; v; v &= v - 1) last[lobit(v)] = (int64_t)x;
+        }
+        if ((int32_t)P.order.size() > ct.begin) {
+            ct.end = (int32_t)P.order.size();
+            P.tiles.push_back(ct);
+        }
+        P.final_l2p = l2p;
+    }
+    if (P.tiles.empty()) P.final_l2p = l2p_init;
+    int kl = std::min(o.evc_low_bits, P.nL);
+    int mmax = std::min(o.evc_span, kMaxSpan);
+    const uint64_t localbits = bit(P.nL) - 1;
+    for (auto &T : P.tiles) {
+        std::vector<int32_t> terms(P.order.begin() + T.begin, P.order.begin() + T.end);
+        std::vector<GroupIn> groups;
+        group_terms(terms, p, coeffs, T.l2p, groups);
+        P.tile_pass_begin.push_back((int32_t)P.passes.size());
+        plan_cosets(P, groups, kl, mmax, localbits);
+        P.tile_pass_end.push_back((int32_t)P.passes.size());
+    }
+    return "";
+}
+
+std::string plan_hpsi(int n, const sv_pauli *p, const double *coeffs, size_t nterms, const PlanOptions &o,
+                      const std::vector<int32_t> &l2p, EvcPlan &P) {
+    P = EvcPlan();
+    P.n = n; P.g = 0; P.nL = n;
+    P.init_l2p = l2p;
+    P.final_l2p = l2p;
+    P.term_slot.assign(nterms, -1);
+    Tile t;
+    t.begin = 0;
+    for (size_t i = 0; i < nterms; ++i) P.order.push_back((int32_t)i);
+    t.end = (int32_t)nterms;
+    t.local_mask = bit(n) - 1;
+    t.l2p = l2p;
+    P.tiles.push_back(t);
+    std::vector<GroupIn> groups;
+    group_terms(P.order, p, coeffs, l2p, groups);
+    P.tile_pass_begin.push_back(0);
+    plan_cosets(P, groups, std::min(o.evc_low_bits, n), std::min(o.evc_span, kMaxSpan), bit(n) - 1);
+    P.tile_pass_end.push_back((int32_t)P.passes.size());
+    return "";
+}
+
+void permutation_swaps(const std::vector<int32_t> &from, const std::vector<int32_t> &to,
+                       std::vector<std::vector<int32_t>> &sets) {
+    int n = (int)from.size();
+    std::vector<int32_t> pi(n, -1);            // physical bit p (layout from) -> physical bit in `to`
+    for (int q = 0; q < n; ++q) pi[from[q]] = to[q];
+    std::vector<int32_t> A, Bs;
+    std::vector<char> seen(n, 0);
+    for (int s = 0; s < n; ++s) {
+        if (seen[s] || pi[s] == s) { seen[s] = 1; continue; }
+        std::vector<int32_t> cyc;
+        for (int c = s; !seen[c]; c = pi[c]) { seen[c] = 1; cyc.push_back(c); }
+        int k = (int)cyc.size();
+        // A: c_i <-> c_{-i};  B: c_i <-> c_{1-i}; B o A maps c_i -> c_{i+1}
+        for (int i = 1; i < k; ++i) {
+            int j = (k - i) % k;
+            if (i < j) { A.push_back(cyc[i]); A.push_back(cyc[j]); }
+        }
+        for (int i = 0; i < k; ++i) {
+            int j = ((1 - i) % k + k) % k;
+            if (i < j) { Bs.push_back(cyc[i]); Bs.push_back(cyc[j]); }
+        }
+    }
+    sets.clear();
+    if (!A.empty()) sets.push_back(A);
+    if (!Bs.empty()) sets.push_back(Bs);
+}
+
+}  // namespace sv

@@ -1,0 +1,127 @@
+// Internal structures shared by the planner, the kernels and the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+
+namespace sv {
+
+constexpr int kMaxQubits = 40;
+constexpr int kMaxSpan = 8;          // coset dimension limit of an EVC / H|psi> pass
+constexpr int kMaxPassStrings = 512; // strings per EVC pass (shared-memory accumulators)
+constexpr int kMaxPassOps = 256;       // gates per shared-memory pass
+constexpr int kMaxGroupStrings = 256; // distinct Z masks sharing one X/Y mask in one group
+
+// ---------------------------------------------------------------- planning --
+
+// One schedulable operator: a gate (QSU) or a Pauli string (EVC).
+struct Op {
+    int32_t kind = 0, nq = 0;
+    int32_t q[4] = {-1, -1, -1, -1};
+    int32_t param = -1, mat = -1;
+    uint64_t tmask = 0;   // logical targets T(op)
+};
+
+// A tile of Sec. IV: operators applied under one qubit mapping.
+struct Tile {
+    int32_t begin = 0, end = 0;      // range of the schedule (order)
+    uint64_t local_mask = 0;         // logical local set Q_L
+    std::vector<int32_t> pairs;      // QR before the tile: (local phys, global phys) pairs
+    std::vector<int32_t> l2p;        // layout in force during the tile
+};
+
+// Device-side gate of a pass: kind, targets as TILE-LOCAL bit positions.
+struct DevOp {
+    int32_t kind;
+    int8_t t[4];
+    int32_t gate;     // index in the caller's gate list (coefficient / gradient slot)
+    int32_t mat;      // complex offset into the matrix array, or -1
+};
+
+// One shared-memory pass of K-GATE / K-ADJ.
+struct GatePass {
+    int32_t tile = 0;
+    int32_t k = 0, nlow = 0;          // staged bits, of which the nlow lowest are contiguous
+    uint64_t bits = 0;                // physical staged bits
+    int32_t op_begin = 0, op_end = 0; // into QsuPlan::ops
+};
+
+struct QsuPlan {
+    int n = 0, g = 0, nL = 0;
+    std::vector<int32_t> order;       // schedule g at tile granularity
+    std::vector<Tile> tiles;
+    std::vector<GatePass> passes;
+    std::vector<DevOp> ops;           // pass operations, pass by pass, in execution order
+    std::vector<int32_t> init_l2p, final_l2p;
+    int32_t nqr() const {
+        int32_t c = 0;
+        for (auto &t : tiles) c += t.pairs.empty() ? 0 : 1;
+        return c;
+    }
+};
+
+// EVC / H|psi>: strings grouped by physical X/Y mask, groups packed into
+// coset passes (see kernels).
+struct EvcString {
+    uint64_t z;        // physical Z/Y mask
+    int32_t nY;        // |x & z| mod 4 relevant
+    double coef;       // summed coefficient of the merged terms
+};
+struct EvcGroup {
+    uint64_t x;        // physical X/Y mask
+    uint32_t X;        // partner offset inside the coset tile: (c << kl) | (x & (2^kl - 1))
+    int32_t s_begin, s_end;   // strings (slots)
+};
+struct CosetPass {
+    int32_t kl = 0, m = 0;
+    uint64_t basis[kMaxSpan] = {};    // span vectors over bits >= kl, reduced
+    int32_t pivot[kMaxSpan] = {};
+    int32_t g_begin = 0, g_end = 0;   // groups
+    int32_t s_begin = 0, s_end = 0;   // strings (slots), contiguous
+};
+
+struct EvcPlan {
+    int n = 0, g = 0, nL = 0;
+    std::vector<int32_t> order;       // term order at tile granularity
+    std::vector<Tile> tiles;
+    std::vector<int32_t> tile_pass_begin, tile_pass_end;
+    std::vector<CosetPass> passes;
+    std::vector<EvcGroup> groups;
+    std::vector<EvcString> strings;   // slots
+    std::vector<int32_t> term_slot;   // per input term
+    std::vector<int32_t> init_l2p, final_l2p;
+    int32_t nqr() const {
+        int32_t c = 0;
+        for (auto &t : tiles) c += t.pairs.empty() ? 0 : 1;
+        return c;
+    }
+};
+
+struct PlanOptions {
+    int tile_bits = 12, low_bits = 5;
+    int evc_low_bits = 7, evc_span = 6;
+    bool pad_highest = true;
+};
+
+// Returns an empty string on success, else the error message.
+std::string validate_gates(int n, const sv_gate *gates, size_t m, size_t np, size_t nmats);
+std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy,
+                     const PlanOptions &o, const std::vector<int32_t> &l2p_init, QsuPlan &out);
+std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size_t nterms,
+                     bool lazy, const PlanOptions &o, const std::vector<int32_t> &l2p_init,
+                     EvcPlan &out);
+// H|psi> grouping: one tile, no QR, cosets over all n bits.
+std::string plan_hpsi(int n, const sv_pauli *p, const double *coeffs, size_t nterms,
+                      const PlanOptions &o, const std::vector<int32_t> &l2p, EvcPlan &out);
+// Write a bit permutation from layout `from` to layout `to` as at most two
+// sets of disjoint physical bit swaps (every permutation is a product of two
+// involutions).
+void permutation_swaps(const std::vector<int32_t> &from, const std::vector<int32_t> &to,
+                       std::vector<std::vector<int32_t>> &swap_sets);
+
+uint64_t hash_bytes(const void *p, size_t n, uint64_t h = 1469598103934665603ull);
+
+}  // namespace sv

@@ -1,0 +1,242 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element,
+on seeded inputs.  Tolerances: complex128 amplitudes 1e-12 max-abs;
+complex64 amplitudes 2e-5 max-abs (FP32 gate math over a few hundred gates);
+expectations, energies and gradients within 1e-4 * sum|a_t| (the stated
+bound for FP32 state with FP64 accumulation)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import grad as ograd
+from oracle import planner as P
+from paper_2410_04252_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+sv = pytest.importorskip("paper_2410_04252_gb300.sv")
+
+AMP_TOL = {sv.C64: 2e-5, sv.C128: 1e-12}
+
+
+def l1(h):
+    return float(np.abs(h.coeffs).sum())
+
+
+def oracle_state(circ, params, init):
+    return oracle.apply_circuit(oracle.basis_state(circ.n, init), circ, params)
+
+
+def mixed_circuit(n, m, seed, with_mats=True):
+    kinds = (W.RY, W.RZ, W.CZ, W.GIVENS, W.DEXC) + ((W.MAT1, W.MAT2, W.MAT4) if with_mats else ())
+    c = W.random_circuit(n, m, seed, kinds)
+    # matrices for MAT gates
+    offs, mats = 0, []
+    for i in range(c.m):
+        k = int(c.kinds[i])
+        if k in (W.MAT1, W.MAT2, W.MAT4):
+            dim = 1 << W.GATE_NQ[k]
+            mats.append(W.random_unitary_mats(1, dim, seed * 1000 + i))
+            c.mat[i] = offs
+            offs += dim * dim
+    c.mats = np.concatenate(mats) if mats else np.zeros(0)
+    return c
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("sched", [sv.LAZY, sv.EAGER])
+@pytest.mark.parametrize("n,g", [(6, 2), (9, 3), (12, 2), (14, 4), (15, 0)])
+def test_qsu_random_circuits(dtype, sched, n, g):
+    c = mixed_circuit(n, 60, 17 + n + g)
+    params = W.uniform_params(c.nparams, 3 + n, -math.pi, math.pi)
+    s = sv.StateVector(n, g, dtype)
+    s.reset(5)
+    s.apply_circuit(c, params, sched)
+    # the layout the library ends in is the oracle planner's
+    T = [c.targets(i) for i in range(c.m)]
+    plan = P.flat_tiling(n, T, n - g) if sched == sv.LAZY else P.adhoc_schedule(n, T, n - g)
+    if plan.perms:
+        assert list(s.permutation()) == plan.perms[-1]
+    got = s.get_state(logical=True)
+    ref = oracle_state(c, params, 5)
+    assert np.max(np.abs(got - ref)) < AMP_TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+def test_qsu_paper_ansatze(dtype):
+    for ansatz, n, g, layers in [("hea", 16, 4, 4), ("fabric", 18, 4, 6), ("hea", 20, 6, 2)]:
+        c = W.hea_circuit(n, layers) if ansatz == "hea" else W.fabric_circuit(n, layers)
+        params = W.uniform_params(c.nparams, 7, -math.pi, math.pi)
+        init = 0 if ansatz == "hea" else W.half_filled_index(n)
+        ref = oracle_state(c, params, init)
+        for sched in (sv.LAZY, sv.EAGER):
+            s = sv.StateVector(n, g, dtype)
+            s.reset(init)
+            s.apply_circuit(c, params, sched)
+            got = s.get_state(logical=True)
+            assert np.max(np.abs(got - ref)) < AMP_TOL[dtype] * (4 if dtype == sv.C64 else 1)
+
+
+@pytest.mark.parametrize("tile_bits,low_bits", [(9, 3), (11, 5), (13, 4), (13, 1)])
+def test_qsu_tile_options(tile_bits, low_bits):
+    n, g = 16, 3
+    c = mixed_circuit(n, 80, 5)
+    params = W.uniform_params(c.nparams, 8, -3, 3)
+    o = sv.default_options(sv.C64)
+    o.tile_bits, o.low_bits = tile_bits, low_bits
+    s = sv.StateVector(n, g, sv.C64, options=o)
+    s.reset(3)
+    s.apply_circuit(c, params, sv.LAZY)
+    assert np.max(np.abs(s.get_state() - oracle_state(c, params, 3))) < 2e-5
+
+
+def test_qsu_edge_cases():
+    # empty circuit; n = 4 with g = 0; a circuit using every qubit of n = 5
+    s = sv.StateVector(8, 2, sv.C128)
+    s.reset(77)
+    s.apply_circuit(W._circuit(8, [], 0), np.zeros(0), sv.LAZY)
+    ref = np.zeros(256, complex)
+    ref[77] = 1
+    assert np.max(np.abs(s.get_state() - ref)) == 0
+    c = mixed_circuit(4, 30, 2)
+    p = W.uniform_params(c.nparams, 2, -1, 1)
+    s = sv.StateVector(4, 0, sv.C128)
+    s.reset(0)
+    s.apply_circuit(c, p, sv.LAZY)
+    assert np.max(np.abs(s.get_state() - oracle_state(c, p, 0))) < 1e-12
+    # invalid inputs raise, nothing runs
+    with pytest.raises(sv.SvError):
+        s.apply_circuit(W._circuit(4, [(W.RY, (9,), 0, -1)], 1), np.zeros(1), sv.LAZY)
+    with pytest.raises(sv.SvError):
+        s.apply_circuit(W._circuit(4, [(W.RY, (1,), 0, -1)], 1), np.array([np.nan]), sv.LAZY)
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("sched", [sv.LAZY, sv.EAGER])
+@pytest.mark.parametrize("kind,n,g", [("random", 10, 2), ("random", 14, 3), ("jw", 12, 3), ("jw", 16, 4)])
+def test_evc(dtype, sched, kind, n, g):
+    h = W.random_hamiltonian(n, 64, 31 + n) if kind == "random" else W.jw_hamiltonian(n, 256, 33 + n)
+    x, _ = W.pauli_masks(h)
+    keep = [i for i in range(h.nterms) if bin(int(x[i])).count("1") <= n - g]
+    h = W.Hamiltonian(n, h.letters[keep], h.coeffs[keep])
+    c = W.hea_circuit(n, 2)
+    params = W.uniform_params(c.nparams, 4, 0, 2 * math.pi)
+    psi = oracle_state(c, params, 0)
+    ref_terms = oracle.expect_terms(psi, h).real
+    ref_e = float(np.dot(h.coeffs, ref_terms))
+    s = sv.StateVector(n, g, dtype)
+    s.reset(0)
+    s.apply_circuit(c, params, sv.LAZY)
+    e, pt = s.expect(h, sched)
+    tol = 1e-12 if dtype == sv.C128 else 1e-4 * l1(h)
+    assert abs(e - ref_e) < tol
+    assert np.max(np.abs(pt - ref_terms)) < (1e-12 if dtype == sv.C128 else 2e-5)
+
+
+def test_evc_special_strings_and_keep_layout():
+    n, g = 12, 3
+    L = np.zeros((6, n), np.uint8)
+    L[1, :] = 3                       # Z on every qubit (Z on all global qubits too)
+    L[2, 0] = 1; L[2, n - 1] = 2      # X on a local and Y on a global qubit
+    L[3, :n - g] = 1                  # X on every local qubit (max X/Y count)
+    L[4, 5] = 2
+    L[5, 2] = 1; L[5, 3] = 1; L[5, 11] = 3
+    h = W.Hamiltonian(n, L, np.array([0.5, -1.0, 0.3, 0.7, 1.1, -0.2]))   # row 0: identity
+    c = W.hea_circuit(n, 3)
+    params = W.uniform_params(c.nparams, 9, 0, 2 * math.pi)
+    psi = oracle_state(c, params, 0)
+    ref = oracle.expect_terms(psi, h).real
+    assert abs(ref[0] - 1) < 1e-12
+    s = sv.StateVector(n, g, sv.C128)
+    s.reset(0)
+    s.apply_circuit(c, params, sv.LAZY)
+    before = list(s.permutation())
+    e, pt = s.expect(h, sv.LAZY, keep_layout=True)
+    assert list(s.permutation()) == before
+    np.testing.assert_allclose(pt, ref, atol=1e-12)
+    assert abs(e - np.dot(h.coeffs, ref)) < 1e-12
+    np.testing.assert_allclose(s.get_state(), psi, atol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("kind", ["random", "jw"])
+def test_apply_hamiltonian(dtype, kind):
+    n, g = 13, 3
+    h = W.random_hamiltonian(n, 100, 5) if kind == "random" else W.jw_hamiltonian(n, 200, 6)
+    c = W.hea_circuit(n, 2)
+    params = W.uniform_params(c.nparams, 4, 0, 2 * math.pi)
+    psi = oracle_state(c, params, 0)
+    ref = oracle.apply_hamiltonian(psi, h)
+    s = sv.StateVector(n, g, dtype)
+    s.set_state(psi)
+    e, lam = s.apply_hamiltonian(h)
+    lam = lam.cpu().numpy()
+    tol = 1e-11 if dtype == sv.C128 else 1e-4 * l1(h)
+    assert np.max(np.abs(lam - ref)) < tol
+    assert abs(e - oracle.energy(psi, h)) < tol
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("sched", [sv.LAZY, sv.EAGER])
+def test_adjoint_gradient_hea(dtype, sched):
+    n, g = 10, 3
+    c = W.hea_circuit(n, 3)
+    params = W.uniform_params(c.nparams, 12, 0, 2 * math.pi)
+    h = W.random_hamiltonian(n, 48, 13)
+    ps = ograd.parameter_shift(c, params, h)
+    e_ref = ograd.objective(c, params, h)
+    s = sv.StateVector(n, g, dtype)
+    s.reset(0)
+    e, gr = s.grad(c, params, h, sched)
+    tol = 1e-10 if dtype == sv.C128 else 1e-4 * l1(h)
+    assert abs(e - e_ref) < tol
+    assert np.max(np.abs(gr - ps)) < tol
+    # the sweep returns the state to |psi0>
+    back = s.get_state()
+    assert abs(back[0] - 1) < (1e-10 if dtype == sv.C128 else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+def test_adjoint_gradient_fabric_and_mixed(dtype):
+    n, g = 10, 2
+    c = W.fabric_circuit(n, 4)
+    params = W.uniform_params(c.nparams, 14, -math.pi, math.pi)
+    h = W.jw_hamiltonian(n, 80, 15)
+    init = W.half_filled_index(n)
+    fd = ograd.finite_difference(c, params, h, init)
+    s = sv.StateVector(n, g, dtype)
+    s.reset(init)
+    e, gr = s.grad(c, params, h, sv.LAZY)
+    tol = 1e-7 if dtype == sv.C128 else 1e-4 * l1(h)
+    assert abs(e - ograd.objective(c, params, h, init)) < tol
+    assert np.max(np.abs(gr - fd)) < tol
+    # random circuit with fixed matrices mixed in (no parameters on them)
+    c2 = mixed_circuit(9, 50, 3)
+    p2 = W.uniform_params(c2.nparams, 16, -2, 2)
+    h2 = W.random_hamiltonian(9, 30, 17)
+    fd2 = ograd.finite_difference(c2, p2, h2, 6)
+    s2 = sv.StateVector(9, 2, dtype)
+    s2.reset(6)
+    e2, g2 = s2.grad(c2, p2, h2, sv.EAGER)
+    assert np.max(np.abs(g2 - fd2)) < (1e-7 if dtype == sv.C128 else 1e-4 * l1(h2))
+
+
+def test_vqe_step_matches_parts_and_is_deterministic():
+    n, g = 12, 3
+    c = W.hea_circuit(n, 3)
+    params = W.uniform_params(c.nparams, 21, 0, 2 * math.pi)
+    h = W.random_hamiltonian(n, 64, 22)
+    s = sv.StateVector(n, g, sv.C64)
+    e1, g1, pt1 = s.vqe_step(0, c, params, h, sv.LAZY, per_term=True)
+    e2, g2, pt2 = s.vqe_step(0, c, params, h, sv.LAZY, per_term=True)
+    assert e1 == e2 and np.array_equal(g1, g2) and np.array_equal(pt1, pt2)    # bitwise
+    ps = ograd.parameter_shift(c, params, h)
+    assert np.max(np.abs(g1 - ps)) < 1e-4 * l1(h)
+    assert abs(e1 - ograd.objective(c, params, h)) < 1e-4 * l1(h)
+    e3, g3, _ = s.vqe_step(0, c, params, h, sv.EAGER)
+    assert abs(e3 - e1) < 1e-4 * l1(h)
+    assert np.max(np.abs(g3 - g1)) < 1e-4 * l1(h)
