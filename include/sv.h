@@ -178,9 +178,10 @@ sv_status sv_apply_circuit(sv_handle *h, const sv_gate *gates, size_t m,
  * with ad hoc QRs.  Inside a tile, strings sharing an X/Y mask share one read
  * and masks are packed into coset passes.  per_term (nullable) receives
  * nterms real values <P_t>.  Partial sums are accumulated in FP64 and reduced
- * in a fixed order.  Synchronises.  Errors: EINVAL for masks >= 2^n, NaN
- * coefficients, or (LAZY/EAGER alike) a string with more than n - g X/Y
- * positions, which no virtual-chunk layout can make narrow.
+ * in a fixed order.  A string with more than n - g X/Y positions fits no
+ * virtual-chunk layout (the paper does not treat this case): such strings are
+ * evaluated in one last tile without a QR, pairing amplitudes across chunks.
+ * Synchronises.  Errors: EINVAL for masks >= 2^n or non-finite coefficients.
  */
 sv_status sv_expect(sv_handle *h, const sv_pauli *paulis, const double *coeffs,
                     size_t nterms, sv_schedule sched, uint32_t flags,

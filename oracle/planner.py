@@ -43,6 +43,9 @@ Readings taken where the paper is silent or inconsistent:
   * Eager EVC uses a string's full support T(P) when it fits n_L qubits and
     its X/Y support otherwise (full support alone cannot make such strings
     narrow).
+  * A string with more X/Y positions than local qubits fits no mapping (the
+    paper does not treat this case); both EVC schedules put such strings in
+    one last tile without a QR, whose amplitude pairs cross chunks.
 """
 from __future__ import annotations
 
@@ -283,13 +286,19 @@ def tiling_pauli_strings(n: int, nG: int, xmasks: list[int], l2p=None) -> Plan:
     support (Z on a global qubit becomes a per-chunk sign, Eq. par_exp).
     Strings with identical supports are merged, counted with multiplicity.
     Each step takes the first global set (lexicographic combinations) whose
-    complement holds the most remaining strings."""
+    complement holds the most remaining strings.  Strings with more X/Y
+    positions than local qubits fit no mapping; they form one last tile
+    evaluated without a QR (see wide_tile)."""
     nL = n - nG
     plan = Plan(n, nL)
     l2p = list(range(n)) if l2p is None else list(l2p)
     cur = {q for q in range(n) if l2p[q] < nL}
     groups = {}
+    wide = []
     for i, x in enumerate(xmasks):
+        if bin(int(x)).count("1") > nL:
+            wide.append(i)
+            continue
         groups.setdefault(int(x), []).append(i)
     remaining = dict(groups)
     full = (1 << n) - 1
@@ -307,15 +316,26 @@ def tiling_pauli_strings(n: int, nG: int, xmasks: list[int], l2p=None) -> Plan:
             if best < cnt:
                 best = cnt
                 bestG = gm
-        if bestG is None:
-            raise ValueError("a Pauli string has more X/Y positions than local qubits")
         take = sorted(x for x in remaining if x & bestG == 0)
         tile = sorted(i for x in take for i in remaining[x])
         for x in take:
             del remaining[x]
         QL = {q for q in range(n) if not (full & bestG) >> q & 1}
         l2p, cur = _emit_tile(plan, tile, QL, l2p, cur)
+    wide_tile(plan, wide, l2p, cur)
     return plan
+
+
+def wide_tile(plan: Plan, wide: list[int], l2p, cur) -> None:
+    """Reading for strings whose X/Y support exceeds n_L (the paper's
+    method has no mapping for them): one last tile, no QR, whose pairs
+    (b, b ^ x) cross chunks."""
+    if wide:
+        plan.tiles.append(sorted(wide))
+        plan.order.extend(sorted(wide))
+        plan.locals_.append(frozenset(cur))
+        plan.qrs.append([])
+        plan.perms.append(list(l2p))
 
 
 def eager_evc_targets(n: int, nL: int, xmasks, zmasks) -> list[tuple]:
@@ -330,7 +350,13 @@ def eager_evc_targets(n: int, nL: int, xmasks, zmasks) -> list[tuple]:
 
 
 def evc_adhoc(n: int, nG: int, xmasks, zmasks, l2p=None) -> Plan:
-    """Index-order EVC with ad hoc QRs (the QSU-based baseline's order)."""
+    """Index-order EVC with ad hoc QRs (the QSU-based baseline's order);
+    strings wider than n_L go to one last tile without a QR."""
     nL = n - nG
     T = eager_evc_targets(n, nL, xmasks, zmasks)
-    return adhoc_schedule(n, T, nL, l2p=l2p, order=list(range(len(T))))
+    narrow = [i for i in range(len(T)) if len(T[i]) <= nL]
+    wide = [i for i in range(len(T)) if len(T[i]) > nL]
+    plan = adhoc_schedule(n, T, nL, l2p=l2p, order=narrow)
+    last = plan.perms[-1] if plan.perms else (list(range(n)) if l2p is None else list(l2p))
+    wide_tile(plan, wide, last, {q for q in range(n) if last[q] < nL})
+    return plan

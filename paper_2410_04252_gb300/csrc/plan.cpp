@@ -509,23 +509,23 @@ void for_each_subset_rank(const std::vector<int> &fr, int k, int n, const Binom 
 // lexicographic order) whose complement holds the most remaining strings.
 // Counts are maintained incrementally: a support x adds its multiplicity to
 // every global set disjoint from it.
-std::string tiling_pauli_strings(int n, int nG, const sv_pauli *p, size_t nterms,
+std::string tiling_pauli_strings(int n, int nG, const sv_pauli *p, const std::vector<int32_t> &terms,
                                  std::vector<std::vector<int32_t>> &tiles_terms,
                                  std::vector<uint64_t> &tiles_local) {
     const uint64_t Q = bit(n) - 1;
     std::unordered_map<uint64_t, int32_t> xi;
     std::vector<uint64_t> xs;
     std::vector<std::vector<int32_t>> members;
-    for (size_t t = 0; t < nterms; ++t) {
+    for (int32_t t : terms) {
         uint64_t x = p[t].x;
         if (popc(x) > n - nG) return "a Pauli string has more X/Y positions than local qubits";
         auto it = xi.find(x);
         if (it == xi.end()) {
             xi[x] = (int32_t)xs.size();
             xs.push_back(x);
-            members.push_back({(int32_t)t});
+            members.push_back({t});
         } else {
-            members[it->second].push_back((int32_t)t);
+            members[it->second].push_back(t);
         }
     }
     Binom B(n);
@@ -651,10 +651,14 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
     P.term_slot.assign(nterms, -1);
     std::vector<int32_t> l2p = l2p_init;
     uint64_t cur = local_set(l2p, P.nL);
+    // strings whose X/Y support exceeds n_L fit no mapping: they are kept for
+    // one last tile without a QR whose amplitude pairs cross chunks
+    std::vector<int32_t> narrow, wide;
+    for (size_t t = 0; t < nterms; ++t) (popc(p[t].x) > P.nL ? wide : narrow).push_back((int32_t)t);
     std::vector<std::vector<int32_t>> tt;
     std::vector<uint64_t> tl;
     if (lazy) {
-        std::string err = tiling_pauli_strings(n, g, p, nterms, tt, tl);
+        std::string err = tiling_pauli_strings(n, g, p, narrow, tt, tl);
         if (!err.empty()) return err;
         for (size_t i = 0; i < tt.size(); ++i) {
             Tile t;
@@ -667,14 +671,12 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
             t.l2p = l2p;
             P.tiles.push_back(std::move(t));
         }
-        P.final_l2p = l2p;
     } else {
         // targets: full support when it fits n_L qubits, else the X/Y support
         std::vector<uint64_t> tms(nterms);
         for (size_t t = 0; t < nterms; ++t) {
             uint64_t full = p[t].x | p[t].z;
             tms[t] = popc(full) <= P.nL ? full : p[t].x;
-            if (popc(tms[t]) > P.nL) return "a Pauli string has more X/Y positions than local qubits";
         }
         // the ad hoc rule on masks (a string may have more than 4 targets)
         uint64_t QL = cur;
@@ -683,8 +685,9 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
         ct.begin = 0;
         ct.local_mask = QL;
         ct.l2p = l2p;
-        for (size_t x = 0; x < nterms; ++x) {
-            uint64_t t = tms[x];
+        for (size_t xi = 0; xi < narrow.size(); ++xi) {
+            const int32_t term = narrow[xi];
+            uint64_t t = tms[term];
             if (t & ~QL) {
                 uint64_t inn = t & ~QL;
                 int k = popc(inn);
@@ -708,25 +711,39 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
                 ct.local_mask = QL;
                 ct.l2p = l2p;
             }
-            P.order.push_back((int32_t)x);
-            for (uint64_t v = t; v; v &= v - 1) last[lobit(v)] = (int64_t)x;
+            P.order.push_back(term);
+            for (uint64_t v = t; v; v &= v - 1) last[lobit(v)] = (int64_t)xi;
         }
         if ((int32_t)P.order.size() > ct.begin) {
             ct.end = (int32_t)P.order.size();
             P.tiles.push_back(ct);
         }
-        P.final_l2p = l2p;
+        cur = QL;
     }
+    P.tile_wide.assign(P.tiles.size(), 0);
+    if (!wide.empty()) {
+        Tile t;
+        t.begin = (int32_t)P.order.size();
+        P.order.insert(P.order.end(), wide.begin(), wide.end());
+        t.end = (int32_t)P.order.size();
+        t.local_mask = local_set(l2p, P.nL);
+        t.l2p = l2p;
+        P.tiles.push_back(std::move(t));
+        P.tile_wide.push_back(1);
+    }
+    P.final_l2p = l2p;
     if (P.tiles.empty()) P.final_l2p = l2p_init;
     int kl = std::min(o.evc_low_bits, P.nL);
     int mmax = std::min(o.evc_span, kMaxSpan);
     const uint64_t localbits = bit(P.nL) - 1;
-    for (auto &T : P.tiles) {
+    const uint64_t allbits = bit(n) - 1;
+    for (size_t ti = 0; ti < P.tiles.size(); ++ti) {
+        const Tile &T = P.tiles[ti];
         std::vector<int32_t> terms(P.order.begin() + T.begin, P.order.begin() + T.end);
         std::vector<GroupIn> groups;
         group_terms(terms, p, coeffs, T.l2p, groups);
         P.tile_pass_begin.push_back((int32_t)P.passes.size());
-        plan_cosets(P, groups, kl, mmax, localbits);
+        plan_cosets(P, groups, kl, mmax, P.tile_wide[ti] ? allbits : localbits);
         P.tile_pass_end.push_back((int32_t)P.passes.size());
     }
     return "";

@@ -88,6 +88,7 @@ struct EvcPlan {
     std::vector<int32_t> order;       // term order at tile granularity
     std::vector<Tile> tiles;
     std::vector<int32_t> tile_pass_begin, tile_pass_end;
+    std::vector<char> tile_wide;      // 1: strings wider than n_L, pairs cross chunks
     std::vector<CosetPass> passes;
     std::vector<EvcGroup> groups;
     std::vector<EvcString> strings;   // slots

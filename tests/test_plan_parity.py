@@ -77,9 +77,7 @@ def test_evc_plan_lazy_and_eager(kind):
         g = 1 + seed % 3
         h = (W.random_hamiltonian(n, 40, 40 + seed) if kind == "random"
              else W.jw_hamiltonian(n, 64, 60 + seed))
-        x, z = W.pauli_masks(h)
-        keep = [i for i in range(h.nterms) if bin(int(x[i])).count("1") <= n - g]
-        x, z = x[keep], z[keep]
+        x, z = W.pauli_masks(h)          # includes strings wider than n_L
         rng = W.SplitMix64(70 + seed)
         l2p = list(range(n))
         if seed % 2:
@@ -134,6 +132,7 @@ def test_invalid_inputs_rejected():
     far = W._circuit(4, [(W.RY, (7,), 0, -1)], 1)
     with pytest.raises(sv.SvError):
         sv.plan_qsu(4, 0, far, sv.LAZY)
-    with pytest.raises(sv.SvError):   # a string with more X/Y than local qubits
-        sv.plan_evc(6, 2, [0b111111], [0], sv.LAZY)
+    # a string with more X/Y than local qubits: last tile, no QR
+    p = sv.plan_evc(6, 2, [0b111111, 0b11], [0, 0], sv.LAZY)
+    assert p["order"][-1] == 0 and not p["tiles"][-1]["pairs"]
     del c
