@@ -430,13 +430,24 @@ __device__ __forceinline__ uint64_t sigma_hi(uint64_t b, const SwapArgs &a) {
 }
 
 // Element x moves to x with every paired bit exchanged.  A CTA takes a tile
-// (the run bits plus the partners of paired run bits) and, when pairs lie
-// outside the tile, its partner tile; both are loaded before either is
-// written, so the swap is in place.  Tiles whose pairs agree everywhere are
-// not touched.
+// -- the lowest L index bits (one contiguous run) plus the partners of paired
+// run bits -- and, when pairs lie outside the tile, its partner tile; both
+// are loaded before either is written, so the swap is in place.  Tiles whose
+// pairs agree everywhere are not touched.  Global accesses are 16-byte vectors
+// along the run; shared memory is swizzled so that the bit exchanges of a
+// warp's reads spread over the banks.
+template <typename R>
+__device__ __forceinline__ uint32_t swz(uint32_t j) {
+    // XOR bits 1..3 (c64) or 0..2 (c128) of the index with higher bits: a
+    // bijection that keeps 16-byte pairs of complex64 adjacent
+    if (sizeof(R) == 4) return j ^ ((((j >> 4) ^ (j >> 8)) & 7u) << 1);
+    return j ^ (((j >> 3) ^ (j >> 6)) & 7u);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const SwapArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int VEC = 16 / sizeof(Cx<R>);        // amplitudes per 16-byte access
     const uint32_t T = 1u << a.ntb;
     const uint32_t nh = 1u << (a.ntb - a.L);
     Cx<R> *A = reinterpret_cast<Cx<R> *>(smem);
@@ -445,27 +456,51 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.tb, a.ntb - a.L);
     __syncthreads();
     const uint32_t runmask = (1u << a.L) - 1u;
-    const uint32_t swz = (1u << min(a.L, 5)) - 1u;
     const uint64_t ntiles = 1ull << a.nout;
+    const bool vec = (VEC == 2) && a.L >= 1;
     for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const uint64_t b0 = deposit(ti, a.out, a.nout);
         const uint64_t b1 = sigma_hi(b0, a);
         if (b1 < b0) continue;
         const bool self = (b1 == b0);
         if (self && a.nlo == 0) continue;
-        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
-            const uint64_t off = hioff[j >> a.L] | (j & runmask);
-            const uint32_t s = j ^ ((j >> a.L) & swz);
-            A[s] = psi[b0 | off];
-            if (!self) B[s] = psi[b1 | off];
+        if (vec) {
+            for (uint32_t j = 2 * threadIdx.x; j < T; j += 2 * blockDim.x) {
+                const uint64_t off = hioff[j >> a.L] | (j & runmask);
+                const uint32_t s = swz<R>(j);
+                *reinterpret_cast<float4 *>(&A[s]) = *reinterpret_cast<const float4 *>(&psi[b0 | off]);
+                if (!self) *reinterpret_cast<float4 *>(&B[s]) = *reinterpret_cast<const float4 *>(&psi[b1 | off]);
+            }
+        } else {
+            for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
+                const uint64_t off = hioff[j >> a.L] | (j & runmask);
+                const uint32_t s = swz<R>(j);
+                A[s] = psi[b0 | off];
+                if (!self) B[s] = psi[b1 | off];
+            }
         }
         __syncthreads();
-        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
-            const uint64_t off = hioff[j >> a.L] | (j & runmask);
-            const uint32_t sj = sigma_lo(j, a);
-            const uint32_t s = sj ^ ((sj >> a.L) & swz);
-            psi[b0 | off] = self ? A[s] : B[s];
-            if (!self) psi[b1 | off] = A[s];
+        if (vec) {
+            for (uint32_t j = 2 * threadIdx.x; j < T; j += 2 * blockDim.x) {
+                const uint64_t off = hioff[j >> a.L] | (j & runmask);
+                const uint32_t s0 = swz<R>(sigma_lo(j, a)), s1 = swz<R>(sigma_lo(j + 1, a));
+                const Cx<R> *src = self ? A : B;
+                float4 v;
+                v.x = src[s0].x; v.y = src[s0].y; v.z = src[s1].x; v.w = src[s1].y;
+                *reinterpret_cast<float4 *>(&psi[b0 | off]) = v;
+                if (!self) {
+                    float4 u;
+                    u.x = A[s0].x; u.y = A[s0].y; u.z = A[s1].x; u.w = A[s1].y;
+                    *reinterpret_cast<float4 *>(&psi[b1 | off]) = u;
+                }
+            }
+        } else {
+            for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
+                const uint64_t off = hioff[j >> a.L] | (j & runmask);
+                const uint32_t s = swz<R>(sigma_lo(j, a));
+                psi[b0 | off] = self ? A[s] : B[s];
+                if (!self) psi[b1 | off] = A[s];
+            }
         }
         __syncthreads();
     }
@@ -839,11 +874,21 @@ cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const
     SwapArgs a;
     memset(&a, 0, sizeof(a));
     a.n = n;
-    // run length: 512 bytes
-    a.L = std::min(n, dt == SV_C64 ? 6 : 5);
+    // tile = the longest low run L with L + (partners of paired run bits) <= TB
+    const int TB = dt == SV_C64 ? 12 : 11;
+    int L = std::min(n, TB);
+    for (; L > 1; --L) {
+        int partners = 0;
+        for (int i = 0; i < npairs; ++i) {
+            const int p = std::min(pairs[2 * i], pairs[2 * i + 1]), q = std::max(pairs[2 * i], pairs[2 * i + 1]);
+            if (p < L && q >= L) ++partners;
+        }
+        if (L + partners <= TB) break;
+    }
+    a.L = L;
     int tb[24], ntb = 0;
     for (int i = 0; i < npairs; ++i) {
-        int p = std::min(pairs[2 * i], pairs[2 * i + 1]), q = std::max(pairs[2 * i], pairs[2 * i + 1]);
+        const int p = std::min(pairs[2 * i], pairs[2 * i + 1]), q = std::max(pairs[2 * i], pairs[2 * i + 1]);
         if (q < a.L) {
             a.la[a.nlo] = (int8_t)p; a.lb[a.nlo] = (int8_t)q; ++a.nlo;
         } else if (p < a.L) {
@@ -856,9 +901,9 @@ cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const
     for (int i = 0; i < ntb; ++i) a.tb[i] = (int8_t)tb[i];
     a.ntb = a.L + ntb;
     for (int i = 0; i < npairs; ++i) {
-        int p = std::min(pairs[2 * i], pairs[2 * i + 1]), q = std::max(pairs[2 * i], pairs[2 * i + 1]);
+        const int p = std::min(pairs[2 * i], pairs[2 * i + 1]), q = std::max(pairs[2 * i], pairs[2 * i + 1]);
         if (p < a.L && q >= a.L) {
-            int r = (int)(std::lower_bound(tb, tb + ntb, q) - tb);
+            const int r = (int)(std::lower_bound(tb, tb + ntb, q) - tb);
             a.la[a.nlo] = (int8_t)p; a.lb[a.nlo] = (int8_t)(a.L + r); ++a.nlo;
         }
     }
