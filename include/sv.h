@@ -267,6 +267,27 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch,
                        uint64_t init_index, const sv_options *opt, void *stream,
                        double *energies, double *grads, double *times_ns, sv_stats *stats);
 
+/*
+ * Expectation values without device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc where they need expectation values (their device memory is
+ * owned by another allocator, or an allocation must not synchronise the
+ * device at that point).  It computes per_term[t] = <psi|P_t|psi> (host,
+ * nullable) and energy = sum_t coeffs[t] per_term[t] (host) for the 2^n
+ * amplitudes at state (device, complex64/complex128, taken in index order:
+ * bit q of the index is qubit q), using the library's EVC kernels with all
+ * scratch in one fixed 1 MiB static device array held by every GPU that
+ * loads the library.  At most 256 strings per call; more is EINVAL.  No
+ * cudaMalloc/cudaFree is called.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current:
+ * make that first call before any stream capture.  All calls share the
+ * array; calls whose work overlaps on the GPU race on it.  Synchronises the
+ * stream (cudaStream_t as void*, NULL = legacy default stream).
+ */
+sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, const sv_pauli *paulis,
+                            const double *coeffs, size_t nterms, double *energy, double *per_term,
+                            void *stream);
+
 const char *sv_last_error(void);
 const char *sv_version(void);
 

@@ -598,6 +598,10 @@ sv_status check_handle(const sv_handle *h) {
 
 }  // namespace
 
+namespace sv {
+void set_last_error(const std::string &m) { g_err = m; }
+}  // namespace sv
+
 extern "C" {
 
 void sv_options_default(sv_dtype dt, sv_options *o) {

@@ -125,4 +125,7 @@ void permutation_swaps(const std::vector<int32_t> &from, const std::vector<int32
 
 uint64_t hash_bytes(const void *p, size_t n, uint64_t h = 1469598103934665603ull);
 
+// Thread-local message returned by sv_last_error().
+void set_last_error(const std::string &m);
+
 }  // namespace sv

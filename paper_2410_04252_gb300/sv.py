@@ -110,6 +110,7 @@ EXPORTS = {
     "sv_plan_free": (None, [_vp]),
     "sv_batch_run": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                     _u64, ctypes.POINTER(Options), _vp, _vp, _vp, _vp, ctypes.POINTER(Stats)]),
+    "sv_expect_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _sz, _dp, _vp, _vp]),
     "sv_last_error": (ctypes.c_char_p, []),
     "sv_version": (ctypes.c_char_p, []),
 }
@@ -375,6 +376,21 @@ def plan_evc(n: int, g: int, x, z, schedule: int = LAZY, options: Options | None
         return _plan_dict(p, n, False)
     finally:
         _lib.sv_plan_free(p)
+
+
+def expect_noalloc(state, n: int, dtype: int, paulis, coeffs, stream=None, per_term: bool = True):
+    """sv_expect_noalloc on a device tensor `state` (index order): returns
+    (energy, per-term values).  Allocates no device memory."""
+    import torch
+    coeffs = np.ascontiguousarray(coeffs, np.float64)
+    paulis = np.ascontiguousarray(paulis, np.uint64)
+    st = torch.cuda.current_stream(state.device) if stream is None else stream
+    e = ctypes.c_double(0.0)
+    pt = np.zeros(len(coeffs), np.float64) if per_term else None
+    _check(_lib.sv_expect_noalloc(ctypes.c_void_p(state.data_ptr()), n, dtype, _ptr(paulis), _ptr(coeffs),
+                                  len(coeffs), ctypes.byref(e), _ptr(pt) if pt is not None else None,
+                                  ctypes.c_void_p(st.cuda_stream)))
+    return e.value, pt
 
 
 def version() -> str:
