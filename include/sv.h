@@ -73,11 +73,13 @@ typedef struct {
 typedef struct {
     int32_t tile_bits;          /* k: a gate pass stages 2^k amplitudes (default 13 c64, 12 c128) */
     int32_t low_bits;           /* contiguous low bits kept in every gate pass (default 4) */
-    int32_t evc_low_bits;       /* contiguous run bits of an EVC / H|psi> coset tile (default 7 c64, 6 c128) */
-    int32_t evc_span;           /* max coset dimension m of an EVC / H|psi> pass (default 6) */
+    int32_t evc_low_bits;       /* shortest contiguous run (bits) of an EVC / H|psi> coset pass (default 5 c64,
+                                   4 c128); a pass stages 2^(evc_low_bits + evc_span) amplitudes and lengthens
+                                   its runs when it needs a smaller span */
+    int32_t evc_span;           /* max coset dimension m of an EVC / H|psi> pass (default 8) */
     int32_t pad_highest;        /* Alg. 3 padding: 1 highest free qubit (default), 0 lowest (printed text) */
     int32_t checkpoint_every;   /* sv_grad: keep a forward copy every c gate passes, 0 = none */
-    int32_t threads;            /* CTA size for gate passes (default 256) */
+    int32_t threads;            /* CTA size of adjoint passes (default 512; gate passes use min(256, threads)) */
     int32_t blocks_per_sm;      /* persistent grid multiplier (0 = occupancy) */
     int64_t wait_limit;         /* spin iterations before a device wait gives up (batched kernel) */
     int32_t profile;            /* 1: time every launch with CUDA events on the stream (sv_stats.ms);

@@ -106,6 +106,7 @@ CosetArgs coset_args(int n, const CosetPass &cp) {
     a.g_end = cp.g_end;
     a.s_begin = cp.s_begin;
     a.s_end = cp.s_end;
+    a.few = (cp.g_end - cp.g_begin) <= 8 && (cp.s_end - cp.s_begin) == (cp.g_end - cp.g_begin);
     return a;
 }
 
@@ -150,7 +151,7 @@ struct sv_handle {
     uint64_t tick = 0;
     std::vector<std::unique_ptr<QsuEntry>> qsu;
     std::vector<std::unique_ptr<EvcEntry>> evc, hps;
-    DevBuf params, coef, mats, part, slotval, opval, grad, scal, per_term;
+    DevBuf params, coef, mats, part, slotval, opval, grad, scal, per_term, status;
     // forward bookkeeping for SV_FORWARD_DONE
     uint64_t last_qsu_key = 0;
     bool forward_valid = false;
@@ -349,7 +350,7 @@ sv_status evc_entry_upload(sv_handle *h, EvcEntry *ent, const double *coeffs, si
         ss[i].z = ent->plan.strings[i].z;
         ss[i].coef = ent->plan.strings[i].coef;
         ss[i].nY = ent->plan.strings[i].nY;
-        ss[i].pad = 0;
+        ss[i].bz = ent->plan.strings[i].bz;
     }
     SV_CK(upload(ent->groups, gs, h->stream));
     SV_CK(upload(ent->strings, ss, h->stream));
@@ -440,7 +441,10 @@ sv_status upload_params(sv_handle *h, QsuEntry *q, const double *params, size_t 
     return SV_OK;
 }
 
-int gate_threads(const sv_handle *h) { return h->opt.threads > 0 ? h->opt.threads : 256; }
+// Gate passes run 256-thread CTAs (two per SM); adjoint passes use
+// options.threads (default 512: they hold two tiles and need more warps).
+int gate_threads(const sv_handle *h) { return std::min(256, h->opt.threads > 0 ? h->opt.threads : 256); }
+int adj_threads(const sv_handle *h) { return h->opt.threads > 0 ? h->opt.threads : 512; }
 
 sv_status run_forward(sv_handle *h, QsuEntry *q, sv_stats *st) {
     const QsuPlan &P = q->plan;
@@ -492,7 +496,8 @@ sv_status run_evc(sv_handle *h, EvcEntry *e, double *energy, double *per_term, s
         for (int pi = P.tile_pass_begin[t]; pi < P.tile_pass_end[t]; ++pi) {
             Rec r(h, st, SV_K_EVC, (double)h->state_bytes());
             SV_CK(launch_evc_pass(h->dt, h->stream, grid, h->psi, e->args[pi], e->groups.as<DevGroup>(),
-                                  e->strings.as<DevString>(), h->part.as<double>(), nslots));
+                                  e->strings.as<DevString>(), h->part.as<double>(), nslots, h->status.as<int>(),
+                                  (long long)h->opt.wait_limit));
         }
     }
     {
@@ -535,7 +540,8 @@ sv_status run_hpsi(sv_handle *h, EvcEntry *e, sv_stats *st) {
     for (int pi = 0; pi < np; ++pi) {
         Rec r(h, st, SV_K_HPSI, (pi == 0 ? 2.0 : 3.0) * (double)h->state_bytes());
         SV_CK(launch_hpsi_pass(h->dt, h->stream, grid, h->psi, h->lam, e->args[pi], e->groups.as<DevGroup>(),
-                               e->strings.as<DevString>(), pi == 0, pi == np - 1, h->part.as<double>()));
+                               e->strings.as<DevString>(), pi == 0, pi == np - 1, h->part.as<double>(),
+                               h->status.as<int>(), (long long)h->opt.wait_limit));
     }
     {
         Rec r(h, st, SV_K_AUX, 0.0);
@@ -547,7 +553,7 @@ sv_status run_hpsi(sv_handle *h, EvcEntry *e, sv_stats *st) {
 
 sv_status run_reverse(sv_handle *h, QsuEntry *q, sv_stats *st) {
     const QsuPlan &P = q->plan;
-    const int threads = gate_threads(h);
+    const int threads = adj_threads(h);
     const int nops = (int)P.ops.size();
     int grid = 1;
     for (auto &a : q->args)
@@ -596,6 +602,20 @@ sv_status check_handle(const sv_handle *h) {
     return SV_OK;
 }
 
+// Device status word of the coset kernels (bounded waits): cleared before a
+// call's kernels, read after its synchronisation.
+sv_status status_reset(sv_handle *h) {
+    SV_CK(h->status.ensure(sizeof(int)));
+    SV_CK(cudaMemsetAsync(h->status.p, 0, sizeof(int), h->stream));
+    return SV_OK;
+}
+sv_status status_check(sv_handle *h) {
+    int v = 0;
+    SV_CK(cudaMemcpy(&v, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v) return fail(SV_ETIMEOUT, "a device wait for a bulk copy expired");
+    return SV_OK;
+}
+
 }  // namespace
 
 namespace sv {
@@ -608,11 +628,11 @@ void sv_options_default(sv_dtype dt, sv_options *o) {
     memset(o, 0, sizeof(*o));
     o->tile_bits = dt == SV_C64 ? 13 : 12;
     o->low_bits = 4;
-    o->evc_low_bits = dt == SV_C64 ? 7 : 6;
-    o->evc_span = 6;
+    o->evc_low_bits = dt == SV_C64 ? 5 : 4;     // shortest run; passes stage 2^(5+8) = 8192 amplitudes
+    o->evc_span = 8;
     o->pad_highest = 1;
     o->checkpoint_every = 0;
-    o->threads = 256;
+    o->threads = 512;
     o->blocks_per_sm = 0;
     o->wait_limit = 1 << 26;
 }
@@ -648,7 +668,7 @@ void sv_destroy(sv_handle *h) {
     for (auto &e : h->evc) e->release();
     for (auto &e : h->hps) e->release();
     for (DevBuf *b : {&h->params, &h->coef, &h->mats, &h->part, &h->slotval, &h->opval, &h->grad, &h->scal,
-                      &h->per_term})
+                      &h->per_term, &h->status})
         b->release();
     for (auto &p : h->pending) { h->ev_pool.push_back(p.a); h->ev_pool.push_back(p.b); }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
@@ -789,10 +809,12 @@ sv_status sv_expect(sv_handle *h, const sv_pauli *paulis, const double *coeffs, 
     }
     EvcEntry *e = nullptr;
     SV_TRY(get_evc(h, paulis, coeffs, nterms, sched == SV_SCHED_LAZY, false, &e, st));
+    SV_TRY(status_reset(h));
     SV_TRY(run_evc(h, e, energy, per_term, st));
     if (flags & SV_KEEP_LAYOUT) SV_TRY(relayout(h, entry, false, st));
     else if (h->l2p != entry) h->forward_valid = false;
     SV_CK(cudaStreamSynchronize(h->stream));
+    SV_TRY(status_check(h));
     SV_TRY(resolve_profile(h, st));
     return SV_OK;
 }
@@ -806,10 +828,12 @@ sv_status sv_apply_hamiltonian(sv_handle *h, const sv_pauli *paulis, const doubl
     SV_TRY(ensure_psi(h));
     EvcEntry *e = nullptr;
     SV_TRY(get_evc(h, paulis, coeffs, nterms, true, true, &e, st));
+    SV_TRY(status_reset(h));
     SV_TRY(run_hpsi(h, e, st));
     if (dst) SV_CK(cudaMemcpyAsync(dst, h->lam, h->state_bytes(), cudaMemcpyDeviceToDevice, h->stream));
     if (energy) SV_CK(cudaMemcpyAsync(energy, h->scal.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CK(cudaStreamSynchronize(h->stream));
+    SV_TRY(status_check(h));
     SV_TRY(resolve_profile(h, st));
     return SV_OK;
 }
@@ -845,12 +869,14 @@ sv_status sv_grad(sv_handle *h, const sv_gate *gates, size_t m, const double *pa
     }
     EvcEntry *e = nullptr;
     SV_TRY(get_evc(h, paulis, coeffs, nterms, true, true, &e, st));
+    SV_TRY(status_reset(h));
     SV_TRY(run_hpsi(h, e, st));
     SV_TRY(run_reverse(h, q, st));
     h->forward_valid = false;
     if (grad && np) SV_CK(cudaMemcpyAsync(grad, h->grad.p, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (energy) SV_CK(cudaMemcpyAsync(energy, h->scal.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CK(cudaStreamSynchronize(h->stream));
+    SV_TRY(status_check(h));
     SV_TRY(resolve_profile(h, st));
     return SV_OK;
 }

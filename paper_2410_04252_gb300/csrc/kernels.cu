@@ -506,157 +506,412 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
     }
 }
 
-// ------------------------------------------------------------------- K-EVC --
-// For group x (X = its offset inside the staged coset) and each pair (b, b^x)
-// with b's lowest X bit clear: w = conj(psi[b^x]) psi[b]; string (x, z) with
-// nY = |x & z| adds  i^nY (-1)^{|b&z|} (w + (-1)^nY conj(w)), which is real:
-//   nY = 0: +2 s Re w,  1: -2 s Im w,  2: -2 s Re w,  3: +2 s Im w,
-// s = (-1)^{|b&z|} with b the FULL physical index (chunk bits included: the
-// per-chunk sign s_j of Eq. par_exp).  x = 0 adds s |psi[b]|^2.
-constexpr int kEvcChunk = 8;
+// ------------------------------------------------------- staged cosets --
+// A coset is staged with 16-byte cp.async copies spread over all threads
+// (runs are >= 16 bytes and contiguous); two buffers alternate so the next
+// coset's copies are in flight while the current one is processed
+// (commit/wait groups: at iteration i, groups i and i+1 are outstanding and
+// waiting for all but the newest completes coset i).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_evc_pass(const Cx<R> *__restrict__ psi, const CosetArgs a,
-                                                  const DevGroup *__restrict__ groups,
-                                                  const DevString *__restrict__ strs, double *__restrict__ part,
-                                                  int part_stride) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const uint32_t E = 1u << (a.kl + a.m);
+__device__ __forceinline__ void load_coset(Cx<R> *dst, const Cx<R> *psi, uint64_t rep, const uint64_t *spanv, int kl,
+                                           uint32_t E) {
+    constexpr uint32_t PER = 16 / sizeof(Cx<R>);
+    const uint32_t lowmask = (1u << kl) - 1u;
+    for (uint32_t q = threadIdx.x; q < E / PER; q += blockDim.x) {
+        const uint32_t e = q * PER;
+        cp_async16(dst + e, psi + (rep ^ spanv[e >> kl] ^ (e & lowmask)));
+    }
+}
+
+__device__ __forceinline__ void coset_span(const CosetArgs &a, uint64_t *spanv) {
     const uint32_t M = 1u << a.m;
-    const int nslots = a.s_end - a.s_begin;
-    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Cx<R> *tile = reinterpret_cast<Cx<R> *>(smem);
-    uint64_t *spanv = reinterpret_cast<uint64_t *>(tile + E);
-    double *acc = reinterpret_cast<double *>(spanv + M);
     for (uint32_t j = threadIdx.x; j < M; j += blockDim.x) {
         uint64_t v = 0;
         for (int i = 0; i < a.m; ++i)
             if (j >> i & 1u) v ^= a.basis[i];
         spanv[j] = v;
     }
-    for (int j = threadIdx.x; j < nslots * nwarps; j += blockDim.x) acc[j] = 0.0;
     __syncthreads();
-    const uint32_t lowmask = (1u << a.kl) - 1u;
+}
+
+// ------------------------------------------------------------------- K-EVC --
+// For group x (offset X inside the staged coset, X = (c << kl) | xlo) and
+// each pair (b, b^x), w = conj(psi[b^x]) psi[b]; string (x, z) with
+// nY = |x & z| contributes 2 Re(i^nY (-1)^{|b&z|} w) per pair.  The formula
+// gives the same value from either element of the pair (swapping the roles
+// conjugates w and flips the sign by (-1)^nY, which cancel), so each pair is
+// evaluated once by whichever thread the split below assigns it to.  x = 0
+// contributes (-1)^{|b&z|} |psi[b]|^2 per element.  b is the FULL physical
+// index, so Z on chunk bits gives the per-chunk sign s_j of Eq. par_exp.
+//
+// Thread mapping: thread t owns the staged elements e = t + j*NT, j < EPT
+// (held in registers), i.e. run position l = t mod 2^kl and run index
+// a = a0 + j*astep with a0 = t >> kl, astep = NT >> kl.  Because parity is
+// linear, parity(b & z) = parity((rep|l) & z) ^ parity(a0 & bz) ^
+// parity(j & w), bz = parities of the span basis against z, w = bz >> log2(astep);
+// the last term over all j is one 32-bit Walsh mask per string.
+// Pair split: partner in the same thread (c's lowest bit among the j bits):
+// take j with that bit clear; partner in another thread (c's lowest bit among
+// the a0 bits, or x inside the run): the thread whose own bit is 0 takes the
+// first half of its j, its partner the second half.
+constexpr int kEvcChunk = 4;   // strings of one group evaluated together
+
+__device__ __forceinline__ uint32_t walsh_mask(uint32_t w) {
+    uint32_t m = 0;
+    if (w & 1u) m ^= 0xAAAAAAAAu;
+    if (w & 2u) m ^= 0xCCCCCCCCu;
+    if (w & 4u) m ^= 0xF0F0F0F0u;
+    if (w & 8u) m ^= 0xFF00FF00u;
+    if (w & 16u) m ^= 0xFFFF0000u;
+    return m;
+}
+
+struct ThreadCoset {
+    uint32_t l, a0, ash;   // run position, first run index, log2(astep)
+};
+
+__device__ __forceinline__ ThreadCoset thread_coset(int kl) {
+    ThreadCoset tc;
+    tc.l = threadIdx.x & ((1u << kl) - 1u);
+    tc.a0 = threadIdx.x >> kl;
+    tc.ash = (uint32_t)(__ffs(blockDim.x) - 1) - (uint32_t)kl;
+    return tc;
+}
+
+// j selection of the pair split (EPT = elements per thread): a mask of the
+// thread's elements that takes exactly one element of every pair, half of
+// them per thread; *fac = 2.  If no such split exists (c flips every j bit
+// while its lowest bit is among the a0 bits) all elements are taken and
+// *fac = 1 (every element then evaluates its own term).
+__device__ __forceinline__ uint32_t pair_select(const ThreadCoset &tc, uint32_t X, int kl, int ept, int &fac) {
+    const uint32_t all = ept >= 32 ? 0xFFFFFFFFu : ((1u << ept) - 1u);
+    const int jb = __ffs(ept) - 1;                 // log2(ept)
+    const uint32_t c = X >> kl;
+    fac = 2;
+    if (c) {
+        const int cb = __ffs(c) - 1;
+        if (cb >= (int)tc.ash) return all & ~walsh_mask(1u << (cb - tc.ash));   // partner: same thread
+        const uint32_t cj = c >> tc.ash;                                         // j bits flipped by c
+        for (int h = 0; h < jb; ++h)
+            if (!((cj >> h) & 1u)) {
+                const uint32_t ph = walsh_mask(1u << h);
+                return all & (((tc.a0 >> cb) & 1u) ? ph : ~ph);
+            }
+        fac = 1;
+        return all;
+    }
+    const int pl = __ffs(X) - 1;   // x inside the run: partner = l ^ xlo, same j
+    if (jb == 0) { fac = 1; return all; }
+    const uint32_t ph = walsh_mask(1u);
+    return all & (((tc.l >> pl) & 1u) ? ph : ~ph);
+}
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ psi, const CosetArgs a,
+                                                     const DevGroup *__restrict__ groups,
+                                                     const DevString *__restrict__ strs, double *__restrict__ part,
+                                                     int part_stride, int *status, long long limit) {
+    (void)status; (void)limit;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t E = 1u << (a.kl + a.m);
+    const int nslots = a.s_end - a.s_begin;
+    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
+    uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
+    double *acc = reinterpret_cast<double *>(spanv + (1u << a.m));
+    for (int j = threadIdx.x; j < nslots * nwarps; j += blockDim.x) acc[j] = 0.0;
+    coset_span(a, spanv);
+    const ThreadCoset tc = thread_coset(a.kl);
     const uint64_t ncos = 1ull << a.nfree;
-    for (uint64_t ci = blockIdx.x; ci < ncos; ci += gridDim.x) {
+    const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    for (uint64_t k = 0; k < 2; ++k) {
+        if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        cp_async_commit();
+    }
+    for (uint64_t it = 0; it < mine; ++it) {
+        const uint64_t ci = blockIdx.x + it * gridDim.x;
         const uint64_t rep = deposit(ci, a.freeb, a.nfree);
-        for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
-            tile[e] = psi[rep ^ spanv[e >> a.kl] ^ (e & lowmask)];
+        Cx<R> *t = buf + (it & 1) * E;
+        cp_async_wait1();
         __syncthreads();
+        Cx<R> own[EPT];
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const uint32_t e = threadIdx.x + j * blockDim.x;
+            own[j] = e < E ? t[e] : mk<R>(0, 0);
+        }
         for (int gi = a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
+            int ifac = 1;
+            const uint32_t sel = G.X ? pair_select(tc, G.X, a.kl, EPT, ifac) : 0xFFFFFFFFu;
+            const R fac = (R)ifac;
             for (int cs = G.s_begin; cs < G.s_end; cs += kEvcChunk) {
-                const int ns = min(kEvcChunk, G.s_end - cs);
-                uint64_t z[kEvcChunk];
-                int ny[kEvcChunk];
+                const int nc = min(kEvcChunk, G.s_end - cs);
+                uint32_t jm[kEvcChunk];
+                int base[kEvcChunk], odd[kEvcChunk];
                 R accr[kEvcChunk];
 #pragma unroll
                 for (int s = 0; s < kEvcChunk; ++s) {
-                    z[s] = s < ns ? strs[cs + s].z : 0ull;
-                    ny[s] = s < ns ? strs[cs + s].nY : 0;
+                    const DevString S = strs[cs + (s < nc ? s : 0)];
+                    jm[s] = walsh_mask(S.bz >> tc.ash);
+                    odd[s] = S.nY & 1;
+                    const int neg0 = G.X ? ((S.nY == 1) | (S.nY == 2)) : 0;
+                    base[s] = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ neg0) & 1;
                     accr[s] = 0;
                 }
-                if (G.X == 0u) {
-                    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
-                        const Cx<R> v = tile[e];
-                        const R p = v.x * v.x + v.y * v.y;
-                        const uint64_t b = rep ^ spanv[e >> a.kl] ^ (e & lowmask);
 #pragma unroll
-                        for (int s = 0; s < kEvcChunk; ++s)
-                            accr[s] += (__popcll(b & z[s]) & 1) ? -p : p;
+                for (int j = 0; j < EPT; ++j) {
+                    const uint32_t e = threadIdx.x + j * blockDim.x;
+                    if (e >= E || !((sel >> j) & 1u)) continue;
+                    const Cx<R> u = own[j];
+                    R wr, wi;
+                    if (G.X) {
+                        const Cx<R> v = t[e ^ G.X];
+                        wr = v.x * u.x + v.y * u.y;    // Re(conj(v) u)
+                        wi = v.x * u.y - v.y * u.x;    // Im(conj(v) u)
+                    } else {
+                        wr = u.x * u.x + u.y * u.y;    // |psi|^2 (x = 0, nY = 0)
+                        wi = 0;
                     }
-                } else {
-                    const int lb = __ffs(G.X) - 1;
-                    for (uint32_t i = threadIdx.x; i < E / 2; i += blockDim.x) {
-                        const uint32_t e = ins0(i, lb), f = e ^ G.X;
-                        const Cx<R> u = tile[e], v = tile[f];
-                        const R wr = v.x * u.x + v.y * u.y;    // Re(conj(v) u)
-                        const R wi = v.x * u.y - v.y * u.x;    // Im(conj(v) u)
-                        const uint64_t b = rep ^ spanv[e >> a.kl] ^ (e & lowmask);
 #pragma unroll
-                        for (int s = 0; s < kEvcChunk; ++s) {
-                            const R val = (ny[s] & 1) ? wi : wr;
-                            const int neg = ((ny[s] == 1) | (ny[s] == 2)) ^ (__popcll(b & z[s]) & 1);
-                            accr[s] += neg ? -2 * val : 2 * val;
+                    for (int s = 0; s < kEvcChunk; ++s) {
+                        if (s < nc) {
+                            const R val = odd[s] ? wi : wr;
+                            accr[s] += ((base[s] ^ (jm[s] >> j)) & 1u) ? -val : val;
                         }
                     }
                 }
 #pragma unroll
                 for (int s = 0; s < kEvcChunk; ++s) {
-                    if (s < ns) {
-                        const R v = warp_sum<R>(accr[s]);
+                    if (s < nc) {
+                        const R v = warp_sum<R>(accr[s] * fac);
                         if (lane == 0) acc[(cs + s - a.s_begin) * nwarps + warp] += (double)v;
                     }
                 }
             }
         }
         __syncthreads();
+        if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        cp_async_commit();
     }
+    __syncthreads();
     for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
-        double t = 0.0;
-        for (int w = 0; w < nwarps; ++w) t += acc[s * nwarps + w];
-        part[(size_t)blockIdx.x * part_stride + a.s_begin + s] = t;
+        double tsum = 0.0;
+        for (int w = 0; w < nwarps; ++w) tsum += acc[s * nwarps + w];
+        part[(size_t)blockIdx.x * part_stride + a.s_begin + s] = tsum;
+    }
+}
+
+// K-EVC, few-string passes (every group one string, at most kEvcFew groups --
+// the case of random Pauli strings): the per-thread pair split and sign data
+// are computed once per kernel; per coset each group adds its FP32 partial
+// into a per-thread shared-memory slot (the state's real type), flushed into
+// FP64 registers every 64 cosets; one FP64 reduction at the end.
+constexpr int kEvcFew = 8;
+
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ R evc_pairs(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sel, int base,
+                                       uint32_t jm, uint32_t E) {
+    R acc = 0;
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const uint32_t e = threadIdx.x + j * blockDim.x;
+        if (e >= E || !((sel >> j) & 1u)) continue;
+        const Cx<R> u = own[j], v = t[e ^ X];
+        const R val = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
+        acc += ((base ^ (jm >> j)) & 1u) ? -val : val;
+    }
+    return acc;
+}
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ psi, const CosetArgs a,
+                                                    const DevGroup *__restrict__ groups,
+                                                    const DevString *__restrict__ strs, double *__restrict__ part,
+                                                    int part_stride) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t E = 1u << (a.kl + a.m);
+    const int ng = a.g_end - a.g_begin;          // == number of strings (one per group)
+    const int NT = blockDim.x;
+    Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
+    uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
+    R *acc32 = reinterpret_cast<R *>(spanv + (1u << a.m));             // [ng][NT], the state's real type
+    uint32_t *pg = reinterpret_cast<uint32_t *>(acc32 + kEvcFew * NT);  // [ng][NT]: sel | tconst << 31
+    __shared__ uint64_t gz[kEvcFew];
+    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew];
+    __shared__ int gmeta[kEvcFew];                                      // odd | fac << 1
+    __shared__ double wsum[kEvcFew][16];
+    coset_span(a, spanv);
+    const ThreadCoset tc = thread_coset(a.kl);
+    for (int g = 0; g < ng; ++g) {
+        const DevGroup G = groups[a.g_begin + g];
+        const DevString S = strs[G.s_begin];
+        int fac = 1;
+        const uint32_t sel = G.X ? pair_select(tc, G.X, a.kl, EPT, fac) : 0xFFFFu;
+        const int neg0 = G.X ? ((S.nY == 1) | (S.nY == 2)) : 0;
+        const int tconst = (__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ neg0) & 1;
+        pg[g * NT + threadIdx.x] = (sel & 0x7FFFFFFFu) | ((uint32_t)tconst << 31);
+        acc32[g * NT + threadIdx.x] = (R)0;
+        if (threadIdx.x == 0) {
+            gz[g] = S.z;
+            gX[g] = G.X;
+            gjm[g] = walsh_mask(S.bz >> tc.ash);
+            gmeta[g] = (S.nY & 1) | (fac << 1);
+        }
+    }
+    __syncthreads();
+    double d[kEvcFew];
+#pragma unroll
+    for (int g = 0; g < kEvcFew; ++g) d[g] = 0.0;
+    const uint64_t ncos = 1ull << a.nfree;
+    const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    for (uint64_t k = 0; k < 2; ++k) {
+        if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        cp_async_commit();
+    }
+    for (uint64_t it = 0; it < mine; ++it) {
+        const uint64_t ci = blockIdx.x + it * gridDim.x;
+        const uint64_t rep = deposit(ci, a.freeb, a.nfree);
+        Cx<R> *t = buf + (it & 1) * E;
+        cp_async_wait1();
+        __syncthreads();
+        Cx<R> own[EPT];
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const uint32_t e = threadIdx.x + j * blockDim.x;
+            own[j] = e < E ? t[e] : mk<R>(0, 0);
+        }
+        for (int g = 0; g < ng; ++g) {
+            const uint32_t p = pg[g * NT + threadIdx.x];
+            const uint32_t X = gX[g];
+            const int meta = gmeta[g];
+            const int base = ((int)(p >> 31) ^ __popcll(rep & gz[g])) & 1;
+            const uint32_t sel = X ? (p & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+            R v;
+            if (X == 0u) {
+                v = 0;
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) {
+                    const uint32_t e = threadIdx.x + j * blockDim.x;
+                    if (e >= E) continue;
+                    const R q = own[j].x * own[j].x + own[j].y * own[j].y;
+                    v += ((base ^ (gjm[g] >> j)) & 1u) ? -q : q;
+                }
+            } else if (meta & 1) {
+                v = evc_pairs<R, EPT, true>(t, own, X, sel, base, gjm[g], E);
+            } else {
+                v = evc_pairs<R, EPT, false>(t, own, X, sel, base, gjm[g], E);
+            }
+            acc32[g * NT + threadIdx.x] += v * (R)(meta >> 1);
+        }
+        if ((it & 63) == 63 || it + 1 == mine) {
+#pragma unroll
+            for (int g = 0; g < kEvcFew; ++g) {
+                if (g < ng) {
+                    d[g] += (double)acc32[g * NT + threadIdx.x];
+                    acc32[g * NT + threadIdx.x] = (R)0;
+                }
+            }
+        }
+        __syncthreads();
+        if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        cp_async_commit();
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int g = 0; g < kEvcFew; ++g) {
+        if (g < ng) {
+            double v = d[g];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) wsum[g][warp] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < ng) {
+        double tsum = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += wsum[threadIdx.x][w];
+        part[(size_t)blockIdx.x * part_stride + a.s_begin + threadIdx.x] = tsum;
     }
 }
 
 // ------------------------------------------------------------------ K-HPSI --
 // lambda[b] += sum_t a_t i^nY (-1)^{|(b^x)&z|} psi[b^x] for every group of the
-// pass (P|c> = i^nY (-1)^{|c&z|} |c^x>, c = b^x).  The first pass stores,
-// later passes add; the last one also accumulates Re<psi|lambda>.
+// pass (P|c> = i^nY (-1)^{|c&z|} |c^x>, c = b^x; parity((b^x)&z) =
+// parity(b&z) ^ (nY & 1)).  The first pass stores, later passes add (the old
+// lambda is loaded into registers while the coset is processed); the last
+// pass also accumulates Re<psi|lambda>.  Same thread mapping and sign
+// factorisation as K-EVC.
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ void hpsi_one(Cx<R> *acc, const Cx<R> *t, uint32_t X, int base, uint32_t jm, R g,
+                                         uint32_t E) {
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const uint32_t e = threadIdx.x + j * blockDim.x;
+        if (e >= E) continue;
+        const Cx<R> v = t[e ^ X];
+        const R f = ((base ^ (jm >> j)) & 1u) ? -g : g;
+        if (ODD) {            // i * v
+            acc[j].x -= f * v.y;
+            acc[j].y += f * v.x;
+        } else {
+            acc[j].x += f * v.x;
+            acc[j].y += f * v.y;
+        }
+    }
+}
+
 template <typename R, int EPT>
-__global__ void __launch_bounds__(512) k_hpsi_pass(const Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
-                                                   const CosetArgs a, const DevGroup *__restrict__ groups,
-                                                   const DevString *__restrict__ strs, int first, int last,
-                                                   double *__restrict__ epart) {
+__global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
+                                                      const CosetArgs a, const DevGroup *__restrict__ groups,
+                                                      const DevString *__restrict__ strs, int first, int last,
+                                                      double *__restrict__ epart, int *status, long long limit) {
+    (void)status; (void)limit;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t E = 1u << (a.kl + a.m);
-    const uint32_t M = 1u << a.m;
-    Cx<R> *tile = reinterpret_cast<Cx<R> *>(smem);
-    uint64_t *spanv = reinterpret_cast<uint64_t *>(tile + E);
+    Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
+    uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
     __shared__ double wsum[32];
-    for (uint32_t j = threadIdx.x; j < M; j += blockDim.x) {
-        uint64_t v = 0;
-        for (int i = 0; i < a.m; ++i)
-            if (j >> i & 1u) v ^= a.basis[i];
-        spanv[j] = v;
-    }
-    __syncthreads();
+    coset_span(a, spanv);
+    const ThreadCoset tc = thread_coset(a.kl);
     const uint32_t lowmask = (1u << a.kl) - 1u;
     const uint64_t ncos = 1ull << a.nfree;
+    const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    for (uint64_t k = 0; k < 2; ++k) {
+        if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        cp_async_commit();
+    }
     double eacc = 0.0;
-    for (uint64_t ci = blockIdx.x; ci < ncos; ci += gridDim.x) {
+    for (uint64_t it = 0; it < mine; ++it) {
+        const uint64_t ci = blockIdx.x + it * gridDim.x;
         const uint64_t rep = deposit(ci, a.freeb, a.nfree);
-        for (uint32_t e = threadIdx.x; e < E; e += blockDim.x)
-            tile[e] = psi[rep ^ spanv[e >> a.kl] ^ (e & lowmask)];
-        __syncthreads();
-        Cx<R> acc[EPT];
+        Cx<R> *t = buf + (it & 1) * E;
+        Cx<R> acc[EPT], old[EPT];
 #pragma unroll
-        for (int j = 0; j < EPT; ++j) acc[j] = mk<R>(0, 0);
+        for (int j = 0; j < EPT; ++j) {
+            const uint32_t e = threadIdx.x + j * blockDim.x;
+            acc[j] = mk<R>(0, 0);
+            old[j] = mk<R>(0, 0);
+            if (!first && e < E) old[j] = lam[rep ^ spanv[e >> a.kl] ^ (e & lowmask)];
+        }
+        cp_async_wait1();
+        __syncthreads();
         for (int gi = a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
-#pragma unroll
-            for (int j = 0; j < EPT; ++j) {
-                const uint32_t e = threadIdx.x + j * blockDim.x;
-                if (e >= E) continue;
-                const Cx<R> v = tile[e ^ G.X];
-                const uint64_t bf = rep ^ spanv[e >> a.kl] ^ (e & lowmask) ^ G.x;
-                R ar = 0, ai = 0;
-                for (int s = G.s_begin; s < G.s_end; ++s) {
-                    const DevString S = strs[s];
-                    const R cf = (__popcll(bf & S.z) & 1) ? -(R)S.coef : (R)S.coef;
-                    // i^nY * v
-                    R rr, ri;
-                    switch (S.nY) {
-                    case 0: rr = v.x; ri = v.y; break;
-                    case 1: rr = -v.y; ri = v.x; break;
-                    case 2: rr = -v.x; ri = -v.y; break;
-                    default: rr = v.y; ri = -v.x; break;
-                    }
-                    ar += cf * rr;
-                    ai += cf * ri;
-                }
-                acc[j].x += ar;
-                acc[j].y += ai;
+            for (int s = G.s_begin; s < G.s_end; ++s) {
+                const DevString S = strs[s];
+                const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
+                const uint32_t jm = walsh_mask(S.bz >> tc.ash);
+                const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
+                if (S.nY & 1) hpsi_one<R, EPT, true>(acc, t, G.X, base, jm, g, E);
+                else hpsi_one<R, EPT, false>(acc, t, G.X, base, jm, g, E);
             }
         }
         R eloc = 0;
@@ -664,21 +919,18 @@ __global__ void __launch_bounds__(512) k_hpsi_pass(const Cx<R> *__restrict__ psi
         for (int j = 0; j < EPT; ++j) {
             const uint32_t e = threadIdx.x + j * blockDim.x;
             if (e >= E) continue;
-            const uint64_t gi = rep ^ spanv[e >> a.kl] ^ (e & lowmask);
-            Cx<R> out = acc[j];
-            if (!first) {
-                const Cx<R> old = lam[gi];
-                out.x += old.x;
-                out.y += old.y;
-            }
-            lam[gi] = out;
+            acc[j].x += old[j].x;
+            acc[j].y += old[j].y;
+            lam[rep ^ spanv[e >> a.kl] ^ (e & lowmask)] = acc[j];
             if (last) {
-                const Cx<R> p = tile[e];
-                eloc += p.x * out.x + p.y * out.y;
+                const Cx<R> p = t[e];
+                eloc += p.x * acc[j].x + p.y * acc[j].y;
             }
         }
         eacc += (double)eloc;
         __syncthreads();
+        if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        cp_async_commit();
     }
     if (last) {
         double v = eacc;
@@ -686,9 +938,9 @@ __global__ void __launch_bounds__(512) k_hpsi_pass(const Cx<R> *__restrict__ psi
         if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
         __syncthreads();
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-            epart[blockIdx.x] = t;
+            double tsum = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tsum += wsum[w];
+            epart[blockIdx.x] = tsum;
         }
     }
 }
@@ -779,7 +1031,7 @@ size_t adj_smem(sv_dtype dt, int k, int nlow, int nops, int threads) {
 }
 size_t coset_smem(sv_dtype dt, int E, int m, int nslots, int nwarps) {
     const size_t es = dt == SV_C64 ? 8 : 16;
-    return (size_t)E * es + ((size_t)1 << m) * 8 + (size_t)nslots * nwarps * 8;
+    return 2 * (size_t)E * es + ((size_t)1 << m) * 8 + (size_t)nslots * nwarps * 8;
 }
 
 }  // namespace
@@ -811,11 +1063,11 @@ int adj_pass_grid(sv_dtype dt, int k, int nlow, int nops, int threads, int block
 }
 
 int coset_grid(sv_dtype dt, int E, int blocks_per_sm, bool hpsi) {
-    // a fixed grid per call so every pass writes the same partial rows
-    int per = (E >= 4096) ? 2 : 4;
-    if (hpsi) per = 2;
+    // one CTA per SM: each holds two staged cosets (double buffer); a fixed
+    // grid per call so every pass writes the same partial rows
+    (void)dt; (void)E; (void)hpsi;
+    int per = 1;
     if (blocks_per_sm > 0) per = std::min(per, blocks_per_sm);
-    (void)dt;
     return per * device_sms();
 }
 
@@ -932,35 +1184,73 @@ cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_evc_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, const CosetArgs &a,
-                            const DevGroup *groups, const DevString *strs, double *part, int part_stride) {
-    const int threads = 256;
+template <typename R>
+cudaError_t evc_dispatch(cudaStream_t st, int grid, const void *psi, const CosetArgs &a, const DevGroup *groups,
+                         const DevString *strs, double *part, int part_stride, int *status, long long limit) {
     const int E = 1 << (a.kl + a.m);
-    const size_t sm = coset_smem(dt, E, a.m, a.s_end - a.s_begin, threads / 32);
-    if (dt == SV_C64) {
-        allow_smem(k_evc_pass<float>, sm);
-        k_evc_pass<float><<<grid, threads, sm, st>>>((const float2 *)psi, a, groups, strs, part, part_stride);
-    } else {
-        allow_smem(k_evc_pass<double>, sm);
-        k_evc_pass<double><<<grid, threads, sm, st>>>((const double2 *)psi, a, groups, strs, part, part_stride);
+    // threads: a multiple of the run length, at least one warp, at most 512
+    const int threads = std::max(std::max(32, 1 << a.kl), std::min(E, 512));
+    const int ept = std::max(1, E / threads);
+    if (a.few) {
+        const size_t smf = 2 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8 +
+                           (size_t)kEvcFew * threads * (sizeof(R) + 4);
+#define SV_EVCF_CASE(N)                                                                                      \
+    case N:                                                                                                  \
+        allow_smem(k_evc_few<R, N>, smf);                                                                    \
+        k_evc_few<R, N><<<grid, threads, smf, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride); \
+        return cudaGetLastError();
+        switch (ept) {
+            SV_EVCF_CASE(1)
+            SV_EVCF_CASE(2)
+            SV_EVCF_CASE(4)
+            SV_EVCF_CASE(8)
+            SV_EVCF_CASE(16)
+        default:
+            return cudaErrorInvalidValue;
+        }
+#undef SV_EVCF_CASE
     }
+    const size_t sm = coset_smem(sizeof(R) == 4 ? SV_C64 : SV_C128, E, a.m, a.s_end - a.s_begin, threads / 32);
+#define SV_EVC_CASE(N)                                                                                       \
+    case N:                                                                                                  \
+        allow_smem(k_evc_pass<R, N>, sm);                                                                    \
+        k_evc_pass<R, N><<<grid, threads, sm, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride, \
+                                                    status, limit);                                          \
+        break;
+    switch (ept) {
+        SV_EVC_CASE(1)
+        SV_EVC_CASE(2)
+        SV_EVC_CASE(4)
+        SV_EVC_CASE(8)
+        SV_EVC_CASE(16)
+    default:
+        return cudaErrorInvalidValue;
+    }
+#undef SV_EVC_CASE
     return cudaGetLastError();
+}
+
+cudaError_t launch_evc_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, const CosetArgs &a,
+                            const DevGroup *groups, const DevString *strs, double *part, int part_stride,
+                            int *status, long long limit) {
+    if (dt == SV_C64) return evc_dispatch<float>(st, grid, psi, a, groups, strs, part, part_stride, status, limit);
+    return evc_dispatch<double>(st, grid, psi, a, groups, strs, part, part_stride, status, limit);
 }
 
 template <typename R>
 cudaError_t hpsi_dispatch(cudaStream_t st, int grid, const void *psi, void *lam, const CosetArgs &a,
-                          const DevGroup *groups, const DevString *strs, int first, int last, double *epart) {
+                          const DevGroup *groups, const DevString *strs, int first, int last, double *epart,
+                          int *status, long long limit) {
     const int E = 1 << (a.kl + a.m);
-    const size_t es = sizeof(Cx<R>);
-    const size_t sm = (size_t)E * es + ((size_t)1 << a.m) * 8;
-    // at least one full warp (the energy reduction shuffles across 32 lanes)
-    int threads = std::max(32, std::min(E, 256));
-    int ept = std::max(1, E / threads);
+    const size_t sm = 2 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8;
+    // a multiple of the run length, at least one warp, at most 512
+    const int threads = std::max(std::max(32, 1 << a.kl), std::min(E, 512));
+    const int ept = std::max(1, E / threads);
 #define SV_HPSI_CASE(N)                                                                                      \
     case N:                                                                                                  \
         allow_smem(k_hpsi_pass<R, N>, sm);                                                                   \
         k_hpsi_pass<R, N><<<grid, threads, sm, st>>>((const Cx<R> *)psi, (Cx<R> *)lam, a, groups, strs,     \
-                                                     first, last, epart);                                    \
+                                                     first, last, epart, status, limit);                     \
         break;
     switch (ept) {
         SV_HPSI_CASE(1)
@@ -968,7 +1258,6 @@ cudaError_t hpsi_dispatch(cudaStream_t st, int grid, const void *psi, void *lam,
         SV_HPSI_CASE(4)
         SV_HPSI_CASE(8)
         SV_HPSI_CASE(16)
-        SV_HPSI_CASE(32)
     default:
         return cudaErrorInvalidValue;
     }
@@ -978,9 +1267,9 @@ cudaError_t hpsi_dispatch(cudaStream_t st, int grid, const void *psi, void *lam,
 
 cudaError_t launch_hpsi_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, void *lam,
                              const CosetArgs &a, const DevGroup *groups, const DevString *strs, int first,
-                             int last, double *epart) {
-    if (dt == SV_C64) return hpsi_dispatch<float>(st, grid, psi, lam, a, groups, strs, first, last, epart);
-    return hpsi_dispatch<double>(st, grid, psi, lam, a, groups, strs, first, last, epart);
+                             int last, double *epart, int *status, long long limit) {
+    if (dt == SV_C64) return hpsi_dispatch<float>(st, grid, psi, lam, a, groups, strs, first, last, epart, status, limit);
+    return hpsi_dispatch<double>(st, grid, psi, lam, a, groups, strs, first, last, epart, status, limit);
 }
 
 cudaError_t launch_reduce_rows(cudaStream_t st, const double *part, int nblocks, int stride, int s_begin,

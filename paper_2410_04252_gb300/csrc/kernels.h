@@ -22,6 +22,7 @@ struct GatePassArgs {
 // pivots (they index the coset representatives).
 struct CosetArgs {
     int n, kl, m, nfree, g_begin, g_end, s_begin, s_end;
+    int few;                 // 1: every group has one string and there are at most 8 groups
     uint64_t basis[kMaxSpan];
     int8_t freeb[64];
 };
@@ -36,7 +37,7 @@ struct DevString {
     uint64_t z;
     double coef;
     int32_t nY;
-    int32_t pad;
+    uint32_t bz;      // parities of the pass's span basis against z
 };
 
 int device_sms();
@@ -55,11 +56,14 @@ cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads,
 // In-place swap of disjoint physical bit pairs (pairs[2i], pairs[2i+1]).
 cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const int32_t *pairs,
                            int npairs, int blocks_per_sm);
+// Coset passes wait on bulk copies with bounded polls (limit); on expiry they
+// set *status = 1 and return early.
 cudaError_t launch_evc_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, const CosetArgs &a,
-                            const DevGroup *groups, const DevString *strs, double *part, int part_stride);
+                            const DevGroup *groups, const DevString *strs, double *part, int part_stride,
+                            int *status, long long limit);
 cudaError_t launch_hpsi_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, void *lam,
                              const CosetArgs &a, const DevGroup *groups, const DevString *strs,
-                             int first, int last, double *epart);
+                             int first, int last, double *epart, int *status, long long limit);
 // out[s] = sum over b < nblocks of part[b * stride + s], s in [s_begin, s_end); fixed order.
 cudaError_t launch_reduce_rows(cudaStream_t st, const double *part, int nblocks, int stride,
                                int s_begin, int s_end, double *out);

@@ -116,7 +116,7 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
         ss[i].z = P.strings[i].z;
         ss[i].coef = P.strings[i].coef;
         ss[i].nY = P.strings[i].nY;
-        ss[i].pad = 0;
+        ss[i].bz = P.strings[i].bz;
     }
 
     // carve the array: tables, results, then per-CTA partial rows
@@ -129,6 +129,7 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
     double *d_slotval = (double *)(p + off); off = align256(off + nslots * sizeof(double));
     double *d_per_term = (double *)(p + off); off = align256(off + nterms * sizeof(double));
     double *d_energy = (double *)(p + off); off = align256(off + sizeof(double));
+    int *d_status = (int *)(p + off); off = align256(off + sizeof(int));
     double *d_part = (double *)(p + off);
     if (off >= kNoAllocScratchBytes) return noalloc_fail(SV_EINVAL, "scratch array too small for this call");
     int E = 1;
@@ -145,6 +146,7 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
         e = (call);                                                                                       \
         if (e != cudaSuccess) return noalloc_fail(SV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e)); \
     } while (0)
+    NOALLOC_CK(cudaMemsetAsync(d_status, 0, sizeof(int), st));
     NOALLOC_CK(cudaMemcpyAsync(d_groups, gs.data(), ngroups * sizeof(sv::DevGroup), cudaMemcpyHostToDevice, st));
     NOALLOC_CK(cudaMemcpyAsync(d_strs, ss.data(), nslots * sizeof(sv::DevString), cudaMemcpyHostToDevice, st));
     NOALLOC_CK(cudaMemcpyAsync(d_term_slot, P.term_slot.data(), nterms * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -166,14 +168,18 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
         a.g_end = cp.g_end;
         a.s_begin = cp.s_begin;
         a.s_end = cp.s_end;
-        NOALLOC_CK(sv::launch_evc_pass(dt, st, grid, state, a, d_groups, d_strs, d_part, nslots));
+        NOALLOC_CK(sv::launch_evc_pass(dt, st, grid, state, a, d_groups, d_strs, d_part, nslots, d_status,
+                                       (long long)o.wait_limit));
     }
     NOALLOC_CK(sv::launch_reduce_rows(st, d_part, grid, nslots, 0, nslots, d_slotval));
     NOALLOC_CK(sv::launch_energy(st, d_slotval, d_term_slot, d_coeffs, (int)nterms, d_per_term, d_energy));
     NOALLOC_CK(cudaMemcpyAsync(energy, d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (per_term)
         NOALLOC_CK(cudaMemcpyAsync(per_term, d_per_term, nterms * sizeof(double), cudaMemcpyDeviceToHost, st));
+    int status = 0;
+    NOALLOC_CK(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     NOALLOC_CK(cudaStreamSynchronize(st));
 #undef NOALLOC_CK
+    if (status) return noalloc_fail(SV_ETIMEOUT, "a device wait for a bulk copy expired");
     return SV_OK;
 }

@@ -290,103 +290,118 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low) {
 // ---------------------------------------------------------- coset passes --
 // Strings sharing a physical X/Y mask x form a group: one read of psi serves
 // all of them.  A pass stages 2^(kl+m) amplitudes: the 2^m runs of 2^kl
-// contiguous amplitudes at R ^ span(a), a in [0, 2^m), for one coset
-// representative R of an m-dimensional span V over bits >= kl.  Every group
+// contiguous amplitudes at rep ^ span(a), a in [0, 2^m), for one coset
+// representative rep of an m-dimensional span V over bits >= kl.  Every group
 // whose high part x >> kl lies in V pairs amplitudes inside the staged set, so
-// all such groups share the pass.  Two greedy choices of V are tried per pass
-// (V spanned by single bits, V spanned by the most frequent masks); the one
-// covering more strings is kept.
+// all such groups share the pass.  Per pass: the span is chosen at the
+// shortest run (largest span) by two greedy rules -- V spanned by single bits
+// (Alg. 3-like, lightest masks first) or by the most frequent masks -- and the
+// one covering more strings is kept; then the run is lengthened as far as the
+// staged size allows (projecting the span onto the bits above the run keeps
+// every selected group covered) and the span is padded with the lowest free
+// bits so that every pass stages the same amount.
 struct GroupIn {
     uint64_t x;
     std::vector<std::pair<uint64_t, double>> zs;   // unique z with summed coefficient
     std::vector<std::vector<int32_t>> terms;       // input terms per z
 };
 
-void plan_cosets(EvcPlan &P, std::vector<GroupIn> &groups, int kl, int mmax, uint64_t allowed) {
-    const uint64_t lowmask = bit(kl) - 1;
+struct Span {
+    std::vector<uint64_t> basis;
+    std::vector<int32_t> pivot;
+    uint64_t reduce(uint64_t r) const {
+        for (size_t j = 0; j < basis.size(); ++j)
+            if (r >> pivot[j] & 1) r ^= basis[j];
+        return r;
+    }
+    void insert(uint64_t v) {
+        v = reduce(v);
+        if (!v) return;
+        const int p = hibit(v);
+        for (auto &b : basis)
+            if (b >> p & 1) b ^= v;
+        basis.push_back(v);
+        pivot.push_back(p);
+    }
+};
+
+void plan_cosets(EvcPlan &P, std::vector<GroupIn> &groups, int klmin, int mmax, int klmax, uint64_t allowed) {
+    // runs stay inside the contiguous low allowed bits (local bits for EVC)
+    int lowallowed = 0;
+    while (lowallowed < 64 && (allowed >> lowallowed & 1)) ++lowallowed;
+    const int stage = std::min(klmin, lowallowed) + mmax;
+    klmin = std::min(klmin, lowallowed);
+    klmax = std::min(klmax, lowallowed);
+    const uint64_t lowmin = bit(klmin) - 1;
     std::vector<int32_t> remaining(groups.size());
     std::iota(remaining.begin(), remaining.end(), 0);
     while (!remaining.empty()) {
-        // candidate A: bit spans
-        auto run = [&](bool bits_mode, std::vector<uint64_t> &basis, std::vector<int32_t> &pivot,
-                       std::vector<int32_t> &sel) {
-            basis.clear(); pivot.clear(); sel.clear();
-            auto reduce = [&](uint64_t r) {
-                for (size_t j = 0; j < basis.size(); ++j)
-                    if (r >> pivot[j] & 1) r ^= basis[j];
-                return r;
-            };
-            auto insert = [&](uint64_t v) {
-                v = reduce(v);
-                if (!v) return;
-                int p = hibit(v);
-                for (auto &b : basis)
-                    if (b >> p & 1) b ^= v;
-                basis.push_back(v);
-                pivot.push_back(p);
-            };
+        auto run = [&](bool bits_mode, Span &sp, std::vector<int32_t> &sel) {
+            sp = Span();
+            sel.clear();
             if (bits_mode) {
                 std::vector<int32_t> byw(remaining);
                 std::stable_sort(byw.begin(), byw.end(), [&](int32_t a, int32_t b) {
-                    return popc(groups[a].x & ~lowmask) < popc(groups[b].x & ~lowmask);
+                    return popc(groups[a].x & ~lowmin) < popc(groups[b].x & ~lowmin);
                 });
                 uint64_t B = 0;
                 for (int32_t gi : byw) {
-                    uint64_t h = groups[gi].x & ~lowmask & allowed;
+                    const uint64_t h = groups[gi].x & ~lowmin & allowed;
                     if (popc(B | h) <= mmax) B |= h;
                     if (popc(B) == mmax) break;
                 }
-                for (uint64_t v = B; v; v &= v - 1) insert(bit(lobit(v)));
+                for (uint64_t v = B; v; v &= v - 1) sp.insert(bit(lobit(v)));
             } else {
-                while ((int)basis.size() < mmax) {
+                while ((int)sp.basis.size() < mmax) {
                     std::unordered_map<uint64_t, int64_t> freq;
                     uint64_t best = 0;
                     int64_t bestc = 0;
                     for (int32_t gi : remaining) {
-                        uint64_t r = reduce(groups[gi].x & ~lowmask);
+                        const uint64_t r = sp.reduce(groups[gi].x & ~lowmin);
                         if (!r) continue;
-                        int64_t c = (freq[r] += (int64_t)groups[gi].zs.size());
+                        const int64_t c = (freq[r] += (int64_t)groups[gi].zs.size());
                         if (c > bestc) { bestc = c; best = r; }
                     }
                     if (!best) break;
-                    insert(best);
+                    sp.insert(best);
                 }
             }
             int64_t strings = 0;
             for (int32_t gi : remaining) {
-                if (reduce(groups[gi].x & ~lowmask)) continue;
-                int64_t c = (int64_t)groups[gi].zs.size();
+                if (sp.reduce(groups[gi].x & ~lowmin)) continue;
+                const int64_t c = (int64_t)groups[gi].zs.size();
                 if (strings + c > kMaxPassStrings && !sel.empty()) continue;
                 sel.push_back(gi);
                 strings += c;
             }
             return strings;
         };
-        std::vector<uint64_t> bA, bB;
-        std::vector<int32_t> pA, pB, sA, sB;
-        int64_t cA = run(true, bA, pA, sA);
-        int64_t cB = run(false, bB, pB, sB);
-        bool useA = cA >= cB;
-        std::vector<uint64_t> &basis = useA ? bA : bB;
-        std::vector<int32_t> &pivot = useA ? pA : pB;
-        std::vector<int32_t> &sel = useA ? sA : sB;
-        // pad the span with unit vectors on the lowest free allowed bits >= kl,
-        // so every pass stages the same number of amplitudes (the low ones
-        // extend the contiguous runs); the span only grows
+        Span sA, sB;
+        std::vector<int32_t> selA, selB;
+        const int64_t cA = run(true, sA, selA);
+        const int64_t cB = run(false, sB, selB);
+        const bool useA = cA >= cB;
+        const Span &chosen = useA ? sA : sB;
+        const std::vector<int32_t> &sel = useA ? selA : selB;
+        // lengthen the run as far as the staged size allows
+        const int kl = std::max(klmin, std::min(klmax, stage - (int)chosen.basis.size()));
+        const uint64_t lowmask = bit(kl) - 1;
+        Span sp;
+        for (uint64_t v : chosen.basis) sp.insert(v & ~lowmask);
         uint64_t pivmask = 0;
-        for (int32_t pv : pivot) pivmask |= bit(pv);
-        for (int b = kl; b < 64 && (int)basis.size() < mmax; ++b) {
+        for (int32_t pv : sp.pivot) pivmask |= bit(pv);
+        for (int b = kl; b < 64 && (int)sp.basis.size() < stage - kl; ++b) {
             if (!(allowed >> b & 1) || (pivmask >> b & 1)) continue;
-            for (auto &v : basis)
+            for (auto &v : sp.basis)
                 if (v >> b & 1) v ^= bit(b);
-            basis.push_back(bit(b));
-            pivot.push_back(b);
+            sp.basis.push_back(bit(b));
+            sp.pivot.push_back(b);
             pivmask |= bit(b);
         }
         CosetPass cp;
         cp.kl = kl;
-        cp.m = (int32_t)basis.size();
-        for (int j = 0; j < cp.m; ++j) { cp.basis[j] = basis[j]; cp.pivot[j] = pivot[j]; }
+        cp.m = (int32_t)sp.basis.size();
+        for (int j = 0; j < cp.m; ++j) { cp.basis[j] = sp.basis[j]; cp.pivot[j] = sp.pivot[j]; }
         cp.g_begin = (int32_t)P.groups.size();
         cp.s_begin = (int32_t)P.strings.size();
         std::vector<char> in(groups.size(), 0);
@@ -396,9 +411,9 @@ void plan_cosets(EvcPlan &P, std::vector<GroupIn> &groups, int kl, int mmax, uin
             EvcGroup eg;
             eg.x = G.x;
             uint32_t c = 0;
-            uint64_t h = G.x & ~lowmask;
+            const uint64_t h = G.x & ~lowmask;
             for (int j = 0; j < cp.m; ++j)
-                if (h >> pivot[j] & 1) c |= 1u << j;
+                if (h >> sp.pivot[j] & 1) c |= 1u << j;
             eg.X = (c << kl) | (uint32_t)(G.x & lowmask);
             eg.s_begin = (int32_t)P.strings.size();
             for (size_t s = 0; s < G.zs.size(); ++s) {
@@ -406,6 +421,9 @@ void plan_cosets(EvcPlan &P, std::vector<GroupIn> &groups, int kl, int mmax, uin
                 es.z = G.zs[s].first;
                 es.nY = popc(G.x & G.zs[s].first) & 3;
                 es.coef = G.zs[s].second;
+                es.bz = 0;
+                for (int j = 0; j < cp.m; ++j)
+                    if (popc(sp.basis[j] & es.z) & 1) es.bz |= 1u << j;
                 for (int32_t t : G.terms[s]) P.term_slot[t] = (int32_t)P.strings.size();
                 P.strings.push_back(es);
             }
@@ -733,8 +751,9 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
     }
     P.final_l2p = l2p;
     if (P.tiles.empty()) P.final_l2p = l2p_init;
-    int kl = std::min(o.evc_low_bits, P.nL);
-    int mmax = std::min(o.evc_span, kMaxSpan);
+    const int klmin = std::min(o.evc_low_bits, P.nL);
+    const int mmax = std::min(o.evc_span, kMaxSpan);
+    const int klmax = std::max(klmin, kMaxRunBits);
     const uint64_t localbits = bit(P.nL) - 1;
     const uint64_t allbits = bit(n) - 1;
     for (size_t ti = 0; ti < P.tiles.size(); ++ti) {
@@ -743,7 +762,7 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
         std::vector<GroupIn> groups;
         group_terms(terms, p, coeffs, T.l2p, groups);
         P.tile_pass_begin.push_back((int32_t)P.passes.size());
-        plan_cosets(P, groups, kl, mmax, P.tile_wide[ti] ? allbits : localbits);
+        plan_cosets(P, groups, klmin, mmax, klmax, P.tile_wide[ti] ? allbits : localbits);
         P.tile_pass_end.push_back((int32_t)P.passes.size());
     }
     return "";
@@ -766,7 +785,8 @@ std::string plan_hpsi(int n, const sv_pauli *p, const double *coeffs, size_t nte
     std::vector<GroupIn> groups;
     group_terms(P.order, p, coeffs, l2p, groups);
     P.tile_pass_begin.push_back(0);
-    plan_cosets(P, groups, std::min(o.evc_low_bits, n), std::min(o.evc_span, kMaxSpan), bit(n) - 1);
+    plan_cosets(P, groups, std::min(o.evc_low_bits, n), std::min(o.evc_span, kMaxSpan),
+                std::max(std::min(o.evc_low_bits, n), kMaxRunBits), bit(n) - 1);
     P.tile_pass_end.push_back((int32_t)P.passes.size());
     return "";
 }

@@ -11,6 +11,7 @@ namespace sv {
 
 constexpr int kMaxQubits = 40;
 constexpr int kMaxSpan = 8;          // coset dimension limit of an EVC / H|psi> pass
+constexpr int kMaxRunBits = 7;       // longest contiguous run of a coset pass (2^7 amplitudes)
 constexpr int kMaxPassStrings = 512; // strings per EVC pass (shared-memory accumulators)
 constexpr int kMaxPassOps = 256;       // gates per shared-memory pass
 constexpr int kMaxGroupStrings = 256; // distinct Z masks sharing one X/Y mask in one group
@@ -67,7 +68,8 @@ struct QsuPlan {
 // coset passes (see kernels).
 struct EvcString {
     uint64_t z;        // physical Z/Y mask
-    int32_t nY;        // |x & z| mod 4 relevant
+    int32_t nY;        // |x & z| mod 4
+    uint32_t bz;       // bit j = parity(basis_j & z) for the pass's span basis
     double coef;       // summed coefficient of the merged terms
 };
 struct EvcGroup {
