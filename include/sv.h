@@ -95,7 +95,8 @@ enum { SV_K_GATE = 0,   /* fused gate pass */
        SV_K_ADJ = 4,    /* adjoint reverse pass */
        SV_K_PERM = 5,   /* layout restore (bit-pair swaps) */
        SV_K_AUX = 6,    /* coefficient prep, reductions, basis reset */
-       SV_K_COUNT = 7 };
+       SV_K_BATCH = 7,  /* persistent batched kernel */
+       SV_K_COUNT = 8 };
 
 /* Counters of one call (optional output). */
 typedef struct {
@@ -106,7 +107,6 @@ typedef struct {
     int32_t plan_cache_hit;        /* every plan came from the cache */
     double plan_ms;                /* host planning time (0 on a cache hit) */
     int32_t kernels[SV_K_COUNT];   /* launches per kind */
-    int32_t pad;
     double bytes[SV_K_COUNT];      /* algorithmic bytes per kind: 2S per gate pass,
                                       2(1-2^-s)S per QR of s pairs, S per EVC pass,
                                       2S / 3S per first / later lambda pass, 4S per
@@ -253,14 +253,19 @@ sv_status sv_plan_pass(const sv_plan *p, int32_t i, int32_t *tile, uint64_t *bit
 void sv_plan_free(sv_plan *p);
 
 /*
- * Batched VQE (many small independent states, one persistent launch):
- * state b runs circuit gates[gate_off[b] .. gate_off[b+1]) with parameters
- * params[param_off[b] ..] from |init_index>, then EVC of the shared
- * Hamiltonian and the adjoint gradient, all inside ONE kernel launch whose
- * CTA clusters each own one state at a time.  energies[batch], grads
- * (param_off[batch] entries, laid out like params) and per-state device
- * completion times in ns since launch (times_ns, nullable) are written to
- * host memory.  n <= 20, no virtual chunks.  Synchronises.
+ * Batched VQE (many small independent states, one persistent launch; the
+ * paper has no counterpart -- it is the batching extension): state b runs
+ * circuit gates[gate_off[b] .. gate_off[b+1]) with parameters
+ * params[param_off[b] .. param_off[b+1]) from |init_index>, then
+ * lambda = H|psi> for the shared Hamiltonian with energy Re<psi|lambda>, then
+ * the adjoint gradient -- all inside ONE kernel launch (captured in a CUDA
+ * graph with the reset of its work counter) in which each CTA takes whole
+ * states from an atomic counter, longest circuits first; no CTA waits for
+ * another.  energies[batch] and grads (laid out like params) are written to
+ * host memory; times_ns (nullable, 2*batch entries) receives each state's
+ * device start and end time in ns relative to the earliest start.  n in
+ * [4, 20], no virtual chunks, at most 512 gates per state.  Allocates its
+ * device buffers for the call and frees them before returning.  Synchronises.
  */
 sv_status sv_batch_run(int n, sv_dtype dt, int batch,
                        const sv_gate *gates, const int32_t *gate_off,

@@ -1013,10 +1013,218 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
                        const double *params, const int32_t *param_off, const sv_pauli *paulis, const double *coeffs,
                        size_t nterms, uint64_t init_index, const sv_options *opt, void *stream, double *energies,
                        double *grads, double *times_ns, sv_stats *st) {
-    (void)n; (void)dt; (void)batch; (void)gates; (void)gate_off; (void)params; (void)param_off; (void)paulis;
-    (void)coeffs; (void)nterms; (void)init_index; (void)opt; (void)stream; (void)energies; (void)grads;
-    (void)times_ns; (void)st;
-    return fail(SV_ESTATE, "batched kernel not built yet");
+    stats_clear(st);
+    if (n < 4 || n > 20) return fail(SV_EINVAL, "sv_batch_run: n must be in [4, 20]");
+    if (dt != SV_C64 && dt != SV_C128) return fail(SV_EINVAL, "bad dtype");
+    if (batch < 1 || !gates || !gate_off || !param_off || !energies) return fail(SV_EINVAL, "null argument");
+    if ((nterms && (!paulis || !coeffs)) || (init_index >> n)) return fail(SV_EINVAL, "bad Hamiltonian or init");
+    const uint64_t lim = (1ull << n) - 1;
+    for (size_t t = 0; t < nterms; ++t) {
+        if ((paulis[t].x & ~lim) || (paulis[t].z & ~lim)) return fail(SV_EINVAL, "Pauli mask beyond n qubits");
+        if (!std::isfinite(coeffs[t])) return fail(SV_EINVAL, "non-finite coefficient");
+    }
+    sv_options o;
+    if (opt) o = *opt;
+    else sv_options_default(dt, &o);
+    sv_options d;
+    sv_options_default(dt, &d);
+    o.tile_bits = d.tile_bits;           // the batched kernel stages 2^13 (c64) / 2^12 (c128) amplitudes
+    o.evc_low_bits = d.evc_low_bits;
+    o.evc_span = d.evc_span;
+    if (o.low_bits <= 0) o.low_bits = d.low_bits;
+    const PlanOptions po = plan_options(o);
+    std::vector<int32_t> l2p(n);
+    for (int q = 0; q < n; ++q) l2p[q] = q;
+    // one plan per distinct circuit
+    std::vector<int32_t> state_plan(batch), plan_pass_off{0}, plan_op_off{0}, gparam;
+    std::vector<GatePassArgs> passes;
+    std::vector<DevOp> ops;
+    std::vector<uint64_t> plan_keys;
+    std::vector<int32_t> gsize(batch);
+    auto t0 = std::chrono::steady_clock::now();
+    for (int b = 0; b < batch; ++b) {
+        const int gb = gate_off[b], ge = gate_off[b + 1];
+        const int pb = param_off[b], pe = param_off[b + 1];
+        if (ge < gb || pe < pb) return fail(SV_EINVAL, "offsets must be non-decreasing");
+        const size_t m = (size_t)(ge - gb), np = (size_t)(pe - pb);
+        if ((int)m > batch_max_gates()) return fail(SV_EINVAL, "sv_batch_run: more than 1024 gates in a state");
+        std::string err = validate_gates(n, gates + gb, m, np, 0);
+        if (!err.empty()) return fail(SV_EINVAL, "state " + std::to_string(b) + ": " + err);
+        for (size_t i = 0; i < np; ++i)
+            if (!std::isfinite(params[pb + i])) return fail(SV_EINVAL, "non-finite parameter");
+        for (size_t i = 0; i < m; ++i) {
+            const int k = gates[gb + i].kind;
+            gparam.push_back((k == SV_RY || k == SV_RZ || k == SV_GIVENS || k == SV_DEXC) ? gates[gb + i].param : -1);
+        }
+        gsize[b] = (int)m;
+        const uint64_t key = hash_bytes(gates + gb, m * sizeof(sv_gate));
+        int pi = -1;
+        for (size_t k = 0; k < plan_keys.size(); ++k)
+            if (plan_keys[k] == key) pi = (int)k;
+        if (pi < 0) {
+            QsuPlan P;
+            err = plan_qsu(n, 0, gates + gb, m, true, po, l2p, P);
+            if (!err.empty()) return fail(SV_EINVAL, "state " + std::to_string(b) + ": " + err);
+            if ((int)P.ops.size() > batch_max_ops()) return fail(SV_EINVAL, "sv_batch_run: more than 512 gates in a state");
+            const int obase = (int)ops.size();
+            for (auto &gp : P.passes) {
+                GatePassArgs a = gate_args(n, gp);
+                a.op_begin += obase;
+                a.op_end += obase;
+                passes.push_back(a);
+            }
+            ops.insert(ops.end(), P.ops.begin(), P.ops.end());
+            plan_pass_off.push_back((int32_t)passes.size());
+            plan_op_off.push_back((int32_t)ops.size());
+            pi = (int)plan_keys.size();
+            plan_keys.push_back(key);
+        }
+        state_plan[b] = pi;
+    }
+    EvcPlan H;
+    std::string err = plan_hpsi(n, paulis, coeffs, nterms, po, l2p, H);
+    if (!err.empty()) return fail(SV_EINVAL, "H|psi> plan: " + err);
+    std::vector<CosetArgs> hp;
+    for (auto &cp : H.passes) hp.push_back(coset_args(n, cp));
+    std::vector<DevGroup> gs(H.groups.size());
+    for (size_t i = 0; i < gs.size(); ++i) {
+        gs[i].x = H.groups[i].x;
+        gs[i].X = H.groups[i].X;
+        gs[i].s_begin = H.groups[i].s_begin;
+        gs[i].s_end = H.groups[i].s_end;
+        gs[i].pad = 0;
+    }
+    std::vector<DevString> ss(H.strings.size());
+    for (size_t i = 0; i < ss.size(); ++i) {
+        ss[i].z = H.strings[i].z;
+        ss[i].coef = H.strings[i].coef;
+        ss[i].nY = H.strings[i].nY;
+        ss[i].bz = H.strings[i].bz;
+    }
+    std::vector<int32_t> order(batch);
+    for (int b = 0; b < batch; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return gsize[x] > gsize[y]; });
+    if (st) st->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+
+    cudaStream_t s0 = (cudaStream_t)stream;
+    const int threads = 512;
+    const int grid = std::min(batch, device_sms());
+    const size_t es = dt == SV_C64 ? 8 : 16;
+    std::vector<DevBuf> bufs(16);
+    auto up = [&](int i, const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t e = bufs[i].ensure(std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess || !bytes) return e;
+        return cudaMemcpyAsync(bufs[i].p, src, bytes, cudaMemcpyHostToDevice, s0);
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(s0);
+        for (auto &b : bufs) b.release();
+    };
+    const size_t nparams = (size_t)param_off[batch];
+#define SV_BCK(call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t _e = (call);                                                                      \
+        if (_e != cudaSuccess) {                                                                      \
+            release();                                                                                \
+            return fail(SV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e));                \
+        }                                                                                             \
+    } while (0)
+    SV_BCK(up(0, passes.data(), passes.size() * sizeof(GatePassArgs)));
+    SV_BCK(up(1, plan_pass_off.data(), plan_pass_off.size() * 4));
+    SV_BCK(up(2, ops.data(), ops.size() * sizeof(DevOp)));
+    SV_BCK(up(3, plan_op_off.data(), plan_op_off.size() * 4));
+    SV_BCK(up(4, state_plan.data(), batch * 4));
+    SV_BCK(up(5, order.data(), batch * 4));
+    SV_BCK(up(6, gate_off, (batch + 1) * 4));
+    SV_BCK(up(7, gparam.data(), gparam.size() * 4));
+    SV_BCK(up(8, param_off, (batch + 1) * 4));
+    SV_BCK(up(9, params, nparams * 8));
+    SV_BCK(up(10, hp.data(), hp.size() * sizeof(CosetArgs)));
+    SV_BCK(up(11, gs.data(), gs.size() * sizeof(DevGroup)));
+    SV_BCK(up(12, ss.data(), ss.size() * sizeof(DevString)));
+    SV_BCK(bufs[13].ensure((size_t)grid * 2 * ((size_t)1 << n) * es));
+    SV_BCK(bufs[14].ensure((batch + nparams + 2 * (size_t)batch) * 8 + 64));
+    double *d_energy = bufs[14].as<double>();
+    double *d_grads = d_energy + batch;
+    unsigned long long *d_t = (unsigned long long *)(d_grads + nparams);
+    SV_BCK(bufs[15].ensure(sizeof(int)));
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.nstates = batch;
+    a.nhpass = (int)hp.size();
+    a.init_index = init_index;
+    a.passes = bufs[0].as<GatePassArgs>();
+    a.plan_pass_off = bufs[1].as<int32_t>();
+    a.ops = bufs[2].as<DevOp>();
+    a.plan_op_off = bufs[3].as<int32_t>();
+    a.state_plan = bufs[4].as<int32_t>();
+    a.order = bufs[5].as<int32_t>();
+    a.gate_off = bufs[6].as<int32_t>();
+    a.gparam = bufs[7].as<int32_t>();
+    a.param_off = bufs[8].as<int32_t>();
+    a.params = bufs[9].as<double>();
+    a.hpass = bufs[10].as<CosetArgs>();
+    a.groups = bufs[11].as<DevGroup>();
+    a.strs = bufs[12].as<DevString>();
+    a.work = bufs[13].p;
+    a.energies = d_energy;
+    a.grads = d_grads;
+    a.t_start = d_t;
+    a.t_end = d_t + batch;
+    a.counter = bufs[15].as<int>();
+    // one graph: reset the work counter, then the persistent launch
+    SV_BCK(cudaStreamSynchronize(s0));
+    cudaStream_t cs = nullptr;
+    SV_BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(a.counter, 0, sizeof(int), cs);
+    if (ce == cudaSuccess) ce = launch_batch(dt, cs, grid, threads, a);
+    cudaError_t ce2 = cudaStreamEndCapture(cs, &graph);
+    if (ce == cudaSuccess) ce = ce2;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, cs);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, cs);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, cs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
+    float ms = 0.f;
+    if (ce == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(cs);
+    if (ce != cudaSuccess) {
+        release();
+        return fail(SV_ECUDA, std::string("batched launch: ") + cudaGetErrorString(ce));
+    }
+    std::vector<unsigned long long> tt(2 * (size_t)batch);
+    SV_BCK(cudaMemcpy(energies, d_energy, batch * 8, cudaMemcpyDeviceToHost));
+    if (grads && nparams) SV_BCK(cudaMemcpy(grads, d_grads, nparams * 8, cudaMemcpyDeviceToHost));
+    SV_BCK(cudaMemcpy(tt.data(), d_t, 2 * (size_t)batch * 8, cudaMemcpyDeviceToHost));
+    if (times_ns) {
+        unsigned long long t_min = ~0ull;
+        for (int b = 0; b < batch; ++b) t_min = std::min(t_min, tt[b]);
+        for (int b = 0; b < batch; ++b) {
+            times_ns[2 * b] = (double)(tt[b] - t_min);
+            times_ns[2 * b + 1] = (double)(tt[batch + b] - t_min);
+        }
+    }
+    if (st) {
+        st->launches = 1;
+        st->kernels[SV_K_BATCH] = 1;
+        st->ms[SV_K_BATCH] = ms;
+        st->qsu_passes = (int32_t)passes.size();
+        st->hpsi_passes = (int32_t)hp.size();
+    }
+    release();
+#undef SV_BCK
+    return SV_OK;
 }
 
 }  // extern "C"

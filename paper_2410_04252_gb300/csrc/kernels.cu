@@ -945,6 +945,187 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
     }
 }
 
+// ----------------------------------------------------------------- K-BATCH --
+// Many independent small states in ONE persistent launch.  A CTA takes a whole
+// state at a time from an atomic work counter (states pre-sorted longest
+// first) and runs, on its own workspace: |psi> = |init>, the QSU gate passes
+// of the state's plan (no virtual chunks), lambda = H psi by the coset passes
+// of the shared Hamiltonian with the energy Re<psi|lambda>, and the adjoint
+// reverse sweep with per-gate FP64 gradient partials.  No CTA ever waits for
+// another CTA; every barrier is a __syncthreads inside one CTA.  Per-state
+// start/end device times (globaltimer, ns) give the latency distribution.
+
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr int kBatchMaxOps = 512;      // gate operations per state (smem accumulators)
+constexpr int kBatchMaxGates = 1024;
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int NT = blockDim.x, nwarps = NT >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr uint32_t TILE = sizeof(R) == 4 ? (1u << 13) : (1u << 12);   // staged amplitudes (64 / 64 KiB)
+    Cx<R> *tp = reinterpret_cast<Cx<R> *>(smem);
+    Cx<R> *tl = tp + TILE;
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + TILE);       // 2^9 entries (k - nlow <= 9)
+    double *opacc = reinterpret_cast<double *>(hioff + 512);        // [kBatchMaxOps][nwarps]
+    R *coef = reinterpret_cast<R *>(opacc + (size_t)kBatchMaxOps * nwarps);   // [2 * kBatchMaxGates]
+    __shared__ int s_state;
+    __shared__ double s_red[32];
+    const size_t N = (size_t)1 << a.n;
+    Cx<R> *psi = reinterpret_cast<Cx<R> *>(a.work) + (size_t)blockIdx.x * 2 * N;
+    Cx<R> *lam = psi + N;
+    while (true) {
+        if (threadIdx.x == 0) s_state = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int si = s_state;
+        if (si >= a.nstates) break;
+        const int st = a.order[si];
+        const unsigned long long t0 = globaltimer_ns();
+        const int plan = a.state_plan[st];
+        const int g0 = a.gate_off[st], ng = a.gate_off[st + 1] - g0;
+        const int p0 = a.param_off[st], np = a.param_off[st + 1] - p0;
+        const int o0 = a.plan_op_off[plan], nops = a.plan_op_off[plan + 1] - o0;
+        for (int g = threadIdx.x; g < ng; g += NT) {
+            const int p = a.gparam[g0 + g];
+            double c = 1.0, sn = 0.0;
+            if (p >= 0) sincos(0.5 * a.params[p0 + p], &sn, &c);
+            coef[2 * g] = (R)c;
+            coef[2 * g + 1] = (R)sn;
+        }
+        for (int j = threadIdx.x; j < nops * nwarps; j += NT) opacc[j] = 0.0;
+        for (size_t i = threadIdx.x; i < N; i += NT) psi[i] = mk<R>(i == a.init_index ? 1 : 0, 0);
+        __syncthreads();
+        // ---- QSU
+        for (int pi = a.plan_pass_off[plan]; pi < a.plan_pass_off[plan + 1]; ++pi) {
+            const GatePassArgs &P = a.passes[pi];
+            const uint32_t T = 1u << P.k, nh = 1u << (P.k - P.nlow), lowmask = (1u << P.nlow) - 1u;
+            for (uint32_t j = threadIdx.x; j < nh; j += NT) hioff[j] = deposit(j, P.hi, P.nhi);
+            __syncthreads();
+            for (uint64_t ti = 0; ti < (1ull << P.nout); ++ti) {
+                const uint64_t base = deposit(ti, P.out, P.nout);
+                for (uint32_t j = threadIdx.x; j < T; j += NT) tp[j] = psi[base | hioff[j >> P.nlow] | (j & lowmask)];
+                __syncthreads();
+                for (int o = P.op_begin; o < P.op_end; ++o) {
+                    const DevOp op = a.ops[o];
+                    apply_op<R>(tp, P.k, op, coef, nullptr, false);
+                    __syncthreads();
+                }
+                for (uint32_t j = threadIdx.x; j < T; j += NT) psi[base | hioff[j >> P.nlow] | (j & lowmask)] = tp[j];
+                __syncthreads();
+            }
+        }
+        // ---- lambda = H psi, energy
+        double eacc = 0.0;
+        for (int hp = 0; hp < a.nhpass; ++hp) {
+            const CosetArgs &C = a.hpass[hp];
+            const uint32_t E = 1u << (C.kl + C.m), M = 1u << C.m, lm = (1u << C.kl) - 1u;
+            uint64_t *spanv = hioff;                     // M <= 256 entries
+            for (uint32_t j = threadIdx.x; j < M; j += NT) {
+                uint64_t v = 0;
+                for (int i = 0; i < C.m; ++i)
+                    if (j >> i & 1u) v ^= C.basis[i];
+                spanv[j] = v;
+            }
+            __syncthreads();
+            const ThreadCoset tc = thread_coset(C.kl);
+            for (uint64_t ci = 0; ci < (1ull << C.nfree); ++ci) {
+                const uint64_t rep = deposit(ci, C.freeb, C.nfree);
+                for (uint32_t e = threadIdx.x; e < E; e += NT) tp[e] = psi[rep ^ spanv[e >> C.kl] ^ (e & lm)];
+                Cx<R> acc[EPT];
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) {
+                    const uint32_t e = threadIdx.x + j * NT;
+                    acc[j] = mk<R>(0, 0);
+                    if (hp > 0 && e < E) acc[j] = lam[rep ^ spanv[e >> C.kl] ^ (e & lm)];
+                }
+                __syncthreads();
+                for (int gi = C.g_begin; gi < C.g_end; ++gi) {
+                    const DevGroup G = a.groups[gi];
+                    for (int s = G.s_begin; s < G.s_end; ++s) {
+                        const DevString S = a.strs[s];
+                        const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
+                        const uint32_t jm = walsh_mask(S.bz >> tc.ash);
+                        const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
+                        if (S.nY & 1) hpsi_one<R, EPT, true>(acc, tp, G.X, base, jm, g, E);
+                        else hpsi_one<R, EPT, false>(acc, tp, G.X, base, jm, g, E);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < EPT; ++j) {
+                    const uint32_t e = threadIdx.x + j * NT;
+                    if (e >= E) continue;
+                    lam[rep ^ spanv[e >> C.kl] ^ (e & lm)] = acc[j];
+                    if (hp == a.nhpass - 1) eacc += (double)(tp[e].x * acc[j].x + tp[e].y * acc[j].y);
+                }
+                __syncthreads();
+            }
+        }
+        if (a.nhpass == 0)
+            for (size_t i = threadIdx.x; i < N; i += NT) lam[i] = mk<R>(0, 0);
+        for (int o = 16; o > 0; o >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, o);
+        if (lane == 0) s_red[warp] = eacc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double e = 0.0;
+            for (int w = 0; w < nwarps; ++w) e += s_red[w];
+            a.energies[st] = e;
+        }
+        // ---- adjoint reverse sweep
+        for (int pi = a.plan_pass_off[plan + 1] - 1; pi >= a.plan_pass_off[plan]; --pi) {
+            const GatePassArgs &P = a.passes[pi];
+            const uint32_t T = 1u << P.k, nh = 1u << (P.k - P.nlow), lowmask = (1u << P.nlow) - 1u;
+            __syncthreads();
+            for (uint32_t j = threadIdx.x; j < nh; j += NT) hioff[j] = deposit(j, P.hi, P.nhi);
+            __syncthreads();
+            for (uint64_t ti = 0; ti < (1ull << P.nout); ++ti) {
+                const uint64_t base = deposit(ti, P.out, P.nout);
+                for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                    const uint64_t gi = base | hioff[j >> P.nlow] | (j & lowmask);
+                    tp[j] = psi[gi];
+                    tl[j] = lam[gi];
+                }
+                __syncthreads();
+                for (int o = P.op_end - 1; o >= P.op_begin; --o) {
+                    const DevOp op = a.ops[o];
+                    R g = adjoint_op<R>(tp, tl, P.k, op, coef, nullptr);
+                    if (has_param(op.kind)) {
+                        g = warp_sum<R>(g);
+                        if (lane == 0) opacc[(o - o0) * nwarps + warp] += (double)g;
+                    }
+                    __syncthreads();
+                }
+                for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                    const uint64_t gi = base | hioff[j >> P.nlow] | (j & lowmask);
+                    psi[gi] = tp[j];
+                    lam[gi] = tl[j];
+                }
+                __syncthreads();
+            }
+        }
+        // gradient: per op, then per parameter in a fixed order
+        if (threadIdx.x == 0) {
+            for (int p = 0; p < np; ++p) a.grads[p0 + p] = 0.0;
+            for (int o = 0; o < nops; ++o) {
+                const DevOp op = a.ops[o0 + o];
+                const int p = a.gparam[g0 + op.gate];
+                if (p < 0 || !has_param(op.kind)) continue;
+                double v = 0.0;
+                for (int w = 0; w < nwarps; ++w) v += opacc[o * nwarps + w];
+                a.grads[p0 + p] += v;
+            }
+            a.t_start[st] = t0;
+            a.t_end[st] = globaltimer_ns();
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------ small kernels --
 template <typename R>
 __global__ void k_prep(const int32_t *__restrict__ gparam, const double *__restrict__ params, int m,
@@ -1301,6 +1482,28 @@ cudaError_t launch_copy(sv_dtype dt, cudaStream_t st, void *dst, const void *src
     if (bl < 1) bl = 1;
     if (dt == SV_C64) k_copy<float><<<bl, th, 0, st>>>((float2 *)dst, (const float2 *)src, n);
     else k_copy<double><<<bl, th, 0, st>>>((double2 *)dst, (const double2 *)src, n);
+    return cudaGetLastError();
+}
+
+size_t batch_smem(sv_dtype dt, int threads) {
+    const size_t es = dt == SV_C64 ? 8 : 16;
+    const size_t tile = dt == SV_C64 ? ((size_t)1 << 13) : ((size_t)1 << 12);
+    return 2 * tile * es + 512 * 8 + (size_t)kBatchMaxOps * (threads / 32) * 8 + 2 * (size_t)kBatchMaxGates * (es / 2);
+}
+
+int batch_max_ops() { return kBatchMaxOps; }
+int batch_max_gates() { return kBatchMaxGates; }
+
+cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, const BatchArgs &a) {
+    if (threads != 512) return cudaErrorInvalidValue;
+    const size_t sm = batch_smem(dt, threads);
+    if (dt == SV_C64) {
+        allow_smem(k_batch<float, 16>, sm);
+        k_batch<float, 16><<<grid, threads, sm, st>>>(a);
+    } else {
+        allow_smem(k_batch<double, 8>, sm);
+        k_batch<double, 8><<<grid, threads, sm, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -40,6 +40,30 @@ struct DevString {
     uint32_t bz;      // parities of the pass's span basis against z
 };
 
+// Batched kernel arguments (see K-BATCH in kernels.cu).
+struct BatchArgs {
+    int n, nstates, nhpass, init_pad;
+    uint64_t init_index;
+    const GatePassArgs *passes;      // all plans' gate passes
+    const int32_t *plan_pass_off;    // [nplans + 1]
+    const DevOp *ops;                // all plans' pass operations (gate = index within the state's circuit)
+    const int32_t *plan_op_off;      // [nplans + 1]: first op of each plan (ops are plan-contiguous)
+    const int32_t *state_plan;       // [nstates]
+    const int32_t *order;            // [nstates] processing order
+    const int32_t *gate_off;         // [nstates + 1] into gparam
+    const int32_t *gparam;           // parameter index (within the state's params) per gate, -1 = none
+    const int32_t *param_off;        // [nstates + 1] into params / grads
+    const double *params;
+    const CosetArgs *hpass;          // shared Hamiltonian passes
+    const DevGroup *groups;
+    const DevString *strs;
+    void *work;                      // per CTA: psi, lambda (2^n each)
+    double *energies;                // [nstates]
+    double *grads;                   // like params
+    unsigned long long *t_start, *t_end;
+    int *counter;
+};
+
 int device_sms();
 int gate_pass_grid(sv_dtype dt, int k, int nlow, int nops, int threads, int blocks_per_sm);
 int adj_pass_grid(sv_dtype dt, int k, int nlow, int nops, int threads, int blocks_per_sm);
@@ -74,5 +98,10 @@ cudaError_t launch_scatter(cudaStream_t st, const double *opval, const int32_t *
 cudaError_t launch_energy(cudaStream_t st, const double *slotval, const int32_t *term_slot,
                           const double *coeffs, int nterms, double *per_term, double *energy);
 cudaError_t launch_copy(sv_dtype dt, cudaStream_t st, void *dst, const void *src, size_t n_elems);
+// One persistent launch over all states (512 threads per CTA).
+cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, const BatchArgs &a);
+size_t batch_smem(sv_dtype dt, int threads);
+int batch_max_ops();
+int batch_max_gates();
 
 }  // namespace sv

@@ -51,8 +51,8 @@ class Options(ctypes.Structure):
                 ("wait_limit", ctypes.c_int64), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-K_GATE, K_QR, K_EVC, K_HPSI, K_ADJ, K_PERM, K_AUX = range(7)
-KERNEL_KINDS = ["gate", "qr", "evc", "hpsi", "adj", "perm", "aux"]
+K_GATE, K_QR, K_EVC, K_HPSI, K_ADJ, K_PERM, K_AUX, K_BATCH = range(8)
+KERNEL_KINDS = ["gate", "qr", "evc", "hpsi", "adj", "perm", "aux", "batch"]
 
 
 class Stats(ctypes.Structure):
@@ -61,11 +61,11 @@ class Stats(ctypes.Structure):
                 ("hpsi_passes", ctypes.c_int32), ("adj_passes", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("plan_cache_hit", ctypes.c_int32),
                 ("plan_ms", ctypes.c_double),
-                ("kernels", ctypes.c_int32 * 7), ("pad", ctypes.c_int32),
-                ("bytes", ctypes.c_double * 7), ("ms", ctypes.c_double * 7)]
+                ("kernels", ctypes.c_int32 * 8),
+                ("bytes", ctypes.c_double * 8), ("ms", ctypes.c_double * 8)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("kernels", "bytes", "ms", "pad")}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("kernels", "bytes", "ms")}
         for i, k in enumerate(KERNEL_KINDS):
             d[f"kernels_{k}"] = self.kernels[i]
             d[f"bytes_{k}"] = self.bytes[i]
@@ -391,6 +391,35 @@ def expect_noalloc(state, n: int, dtype: int, paulis, coeffs, stream=None, per_t
                                   len(coeffs), ctypes.byref(e), _ptr(pt) if pt is not None else None,
                                   ctypes.c_void_p(st.cuda_stream)))
     return e.value, pt
+
+
+def batch_run(n: int, dtype: int, circuits, params_list, ham=None, paulis=None, coeffs=None, init_index: int = 0,
+              options: Options | None = None, stream=None):
+    """sv_batch_run over independent states: circuits[b] (workloads.Circuit)
+    with params_list[b].  Returns (energies, list of gradients, times_ns
+    (batch, 2) start/end, Stats)."""
+    import torch
+    if ham is not None:
+        paulis, coeffs = hamiltonian_arrays(ham)
+    coeffs = np.ascontiguousarray(coeffs, np.float64)
+    gates = np.ascontiguousarray(np.concatenate([gate_array(c) for c in circuits]), np.int32)
+    gate_off = np.zeros(len(circuits) + 1, np.int32)
+    gate_off[1:] = np.cumsum([c.m for c in circuits])
+    params = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64) for p in params_list]), np.float64)
+    param_off = np.zeros(len(circuits) + 1, np.int32)
+    param_off[1:] = np.cumsum([len(p) for p in params_list])
+    batch = len(circuits)
+    energies = np.zeros(batch, np.float64)
+    grads = np.zeros(max(params.size, 1), np.float64)
+    times = np.zeros(2 * batch, np.float64)
+    st = Stats()
+    s = torch.cuda.current_stream() if stream is None else stream
+    _check(_lib.sv_batch_run(n, dtype, batch, _ptr(gates), _ptr(gate_off), _ptr(params), _ptr(param_off),
+                             _ptr(paulis), _ptr(coeffs), len(coeffs), int(init_index),
+                             ctypes.byref(options) if options is not None else None, ctypes.c_void_p(s.cuda_stream),
+                             _ptr(energies), _ptr(grads), _ptr(times), ctypes.byref(st)))
+    gl = [grads[param_off[b]:param_off[b + 1]].copy() for b in range(batch)]
+    return energies, gl, times.reshape(batch, 2), st
 
 
 def version() -> str:
