@@ -78,7 +78,9 @@ typedef struct {
                                    its runs when it needs a smaller span */
     int32_t evc_span;           /* max coset dimension m of an EVC / H|psi> pass (default 8) */
     int32_t pad_highest;        /* Alg. 3 padding: 1 highest free qubit (default), 0 lowest (printed text) */
-    int32_t checkpoint_every;   /* sv_grad: keep a forward copy every c gate passes, 0 = none */
+    int32_t checkpoint_every;   /* c > 0: the forward sweep keeps a copy of psi after every c-th gate pass
+                                   (device memory, else pinned host memory) and the adjoint sweep
+                                   re-anchors psi from it instead of the uncomputed value; 0 = none */
     int32_t threads;            /* CTA size of adjoint passes (default 512; gate passes use min(256, threads)) */
     int32_t blocks_per_sm;      /* persistent grid multiplier (0 = occupancy) */
     int64_t wait_limit;         /* spin iterations before a device wait gives up (batched kernel) */

@@ -155,6 +155,19 @@ struct sv_handle {
     // forward bookkeeping for SV_FORWARD_DONE
     uint64_t last_qsu_key = 0;
     bool forward_valid = false;
+    // forward checkpoints (options.checkpoint_every): copies of psi after
+    // selected gate passes of the plan last applied, device or pinned host
+    struct Ckpt { int pass; void *p; bool host; };
+    std::vector<Ckpt> ckpts;
+    uint64_t ckpt_key = 0;
+    void drop_ckpts() {
+        for (auto &c : ckpts) {
+            if (c.host) cudaFreeHost(c.p);
+            else cudaFree(c.p);
+        }
+        ckpts.clear();
+        ckpt_key = 0;
+    }
     // profiling: event pairs of launches not yet resolved
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int kind; cudaEvent_t a, b; };
@@ -446,9 +459,29 @@ sv_status upload_params(sv_handle *h, QsuEntry *q, const double *params, size_t 
 int gate_threads(const sv_handle *h) { return std::min(256, h->opt.threads > 0 ? h->opt.threads : 256); }
 int adj_threads(const sv_handle *h) { return h->opt.threads > 0 ? h->opt.threads : 512; }
 
+// Copy psi after gate pass `pass` into a checkpoint slot: device memory if
+// available, else pinned host memory (the case where the state buffers do not
+// all fit in HBM).
+sv_status take_checkpoint(sv_handle *h, int pass, sv_stats *st) {
+    void *p = nullptr;
+    bool host = false;
+    if (cudaMalloc(&p, h->state_bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        host = true;
+        if (cudaMallocHost(&p, h->state_bytes()) != cudaSuccess)
+            return fail(SV_ENOMEM, "no room for a forward checkpoint on the device or the host");
+    }
+    h->ckpts.push_back({pass, p, host});
+    Rec r(h, st, SV_K_PERM, 2.0 * (double)h->state_bytes());
+    SV_CK(cudaMemcpyAsync(p, h->psi, h->state_bytes(), host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          h->stream));
+    return SV_OK;
+}
+
 sv_status run_forward(sv_handle *h, QsuEntry *q, sv_stats *st) {
     const QsuPlan &P = q->plan;
     const int threads = gate_threads(h);
+    h->drop_ckpts();
     size_t pi = 0;
     for (size_t t = 0; t < P.tiles.size(); ++t) {
         const Tile &T = P.tiles[t];
@@ -462,11 +495,16 @@ sv_status run_forward(sv_handle *h, QsuEntry *q, sv_stats *st) {
             int grid = gate_pass_grid(h->dt, a.k, a.nlow, a.op_end - a.op_begin, threads, h->opt.blocks_per_sm);
             uint64_t ntiles = 1ull << a.nout;
             if ((uint64_t)grid > ntiles) grid = (int)ntiles;
-            Rec r(h, st, SV_K_GATE, 2.0 * (double)h->state_bytes());
-            SV_CK(launch_gate_pass(h->dt, h->stream, grid, threads, h->psi, a, q->ops.as<DevOp>(), h->coef.p,
-                                   h->mats.p));
+            {
+                Rec r(h, st, SV_K_GATE, 2.0 * (double)h->state_bytes());
+                SV_CK(launch_gate_pass(h->dt, h->stream, grid, threads, h->psi, a, q->ops.as<DevOp>(), h->coef.p,
+                                       h->mats.p));
+            }
+            const int c = h->opt.checkpoint_every;
+            if (c > 0 && (int)(pi + 1) % c == 0 && pi + 1 < P.passes.size()) SV_TRY(take_checkpoint(h, (int)pi, st));
         }
     }
+    if (h->opt.checkpoint_every > 0) h->ckpt_key = q->key;
     if (st) {
         st->qsu_tiles = (int32_t)P.tiles.size();
         st->qsu_qrs = P.nqr();
@@ -565,6 +603,13 @@ sv_status run_reverse(sv_handle *h, QsuEntry *q, sv_stats *st) {
     for (int t = (int)P.tiles.size() - 1; t >= 0; --t) {
         for (; pi >= 0 && P.passes[pi].tile == t; --pi) {
             const GatePassArgs &a = q->args[pi];
+            if (h->ckpt_key == q->key)
+                for (auto &c : h->ckpts)
+                    if (c.pass == pi) {   // re-anchor psi at the forward value after this pass
+                        Rec r(h, st, SV_K_PERM, 2.0 * (double)h->state_bytes());
+                        SV_CK(cudaMemcpyAsync(h->psi, c.p, h->state_bytes(),
+                                              c.host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+                    }
             Rec r(h, st, SV_K_ADJ, 4.0 * (double)h->state_bytes());
             SV_CK(launch_adj_pass(h->dt, h->stream, grid, threads, h->psi, h->lam, a, q->ops.as<DevOp>(), h->coef.p,
                                   h->mats.p, h->part.as<double>(), nops));
@@ -670,6 +715,7 @@ void sv_destroy(sv_handle *h) {
     for (DevBuf *b : {&h->params, &h->coef, &h->mats, &h->part, &h->slotval, &h->opval, &h->grad, &h->scal,
                       &h->per_term, &h->status})
         b->release();
+    h->drop_ckpts();
     for (auto &p : h->pending) { h->ev_pool.push_back(p.a); h->ev_pool.push_back(p.b); }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->psi_owned && h->psi) cudaFree(h->psi);
@@ -873,6 +919,10 @@ sv_status sv_grad(sv_handle *h, const sv_gate *gates, size_t m, const double *pa
     SV_TRY(run_hpsi(h, e, st));
     SV_TRY(run_reverse(h, q, st));
     h->forward_valid = false;
+    if (!h->ckpts.empty()) {
+        SV_CK(cudaStreamSynchronize(h->stream));
+        h->drop_ckpts();
+    }
     if (grad && np) SV_CK(cudaMemcpyAsync(grad, h->grad.p, np * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (energy) SV_CK(cudaMemcpyAsync(energy, h->scal.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     SV_CK(cudaStreamSynchronize(h->stream));

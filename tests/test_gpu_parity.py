@@ -237,3 +237,32 @@ def test_vqe_step_matches_parts_and_is_deterministic():
     e3, g3, _ = s.vqe_step(0, c, params, h, sv.EAGER)
     assert abs(e3 - e1) < 1e-4 * l1(h)
     assert np.max(np.abs(g3 - g1)) < 1e-4 * l1(h)
+
+
+@pytest.mark.parametrize("every", [1, 2])
+def test_adjoint_with_forward_checkpoints(every):
+    """Re-anchoring psi from forward checkpoints gives the same gradient and
+    leaves the state at |psi0>; the checkpoints are dropped afterwards."""
+    n, g = 13, 3
+    c = W.hea_circuit(n, 4)
+    params = W.uniform_params(c.nparams, 31, 0, 2 * math.pi)
+    h = W.random_hamiltonian(n, 40, 32)
+    o = sv.default_options(sv.C64)
+    o.tile_bits, o.low_bits = 9, 3            # several passes so checkpoints are taken
+    s0 = sv.StateVector(n, g, sv.C64, options=o)
+    s0.reset(0)
+    e0, g0 = s0.grad(c, params, h, sv.LAZY)
+    o.checkpoint_every = every
+    s1 = sv.StateVector(n, g, sv.C64, options=o)
+    s1.reset(0)
+    e1, g1 = s1.grad(c, params, h, sv.LAZY)
+    st = s1.last_stats
+    assert st.kernels[sv.K_PERM] > 0          # checkpoint copies were made and used
+    assert abs(e1 - e0) < 1e-4 * float(np.abs(h.coeffs).sum())
+    assert np.max(np.abs(g1 - g0)) < 1e-4 * float(np.abs(h.coeffs).sum())
+    ps = ograd.parameter_shift(c, params, h)
+    assert np.max(np.abs(g1 - ps)) < 1e-4 * float(np.abs(h.coeffs).sum())
+    assert abs(s1.get_state()[0] - 1) < 1e-4
+    # vqe_step (forward by sv_apply_circuit, gradient with SV_FORWARD_DONE) uses them too
+    e2, g2, _ = s1.vqe_step(0, c, params, h, sv.LAZY)
+    assert np.max(np.abs(g2 - ps)) < 1e-4 * float(np.abs(h.coeffs).sum())
