@@ -85,6 +85,8 @@ GatePassArgs gate_args(int n, const GatePass &gp) {
         if (!(gp.bits >> b & 1)) a.out[a.nout++] = (int8_t)b;
     a.op_begin = gp.op_begin;
     a.op_end = gp.op_end;
+    a.ph_begin = gp.ph_begin;
+    a.ph_end = gp.ph_end;
     return a;
 }
 
@@ -114,11 +116,11 @@ struct QsuEntry {
     uint64_t key = 0;
     QsuPlan plan;
     std::vector<GatePassArgs> args;
-    DevBuf ops, gparam, csr_off, csr_idx;
+    DevBuf ops, gparam, csr_off, csr_idx, phases;
     int m = 0, np = 0;
     double plan_ms = 0;
     uint64_t last_use = 0;
-    void release() { ops.release(); gparam.release(); csr_off.release(); csr_idx.release(); }
+    void release() { ops.release(); gparam.release(); csr_off.release(); csr_idx.release(); phases.release(); }
 };
 
 struct EvcEntry {
@@ -313,6 +315,7 @@ sv_status get_qsu(sv_handle *h, const sv_gate *gates, size_t m, size_t np, sv_sc
     ent->np = (int)np;
     for (auto &gp : ent->plan.passes) ent->args.push_back(gate_args(h->n, gp));
     SV_CK(upload(ent->ops, ent->plan.ops, h->stream));
+    SV_CK(upload(ent->phases, ent->plan.phases, h->stream));
     std::vector<int32_t> gparam(m);
     for (size_t i = 0; i < m; ++i) gparam[i] = gates[i].param;
     bool parametric_kind[8] = {true, true, false, true, true, false, false, false};
@@ -495,7 +498,12 @@ sv_status run_forward(sv_handle *h, QsuEntry *q, sv_stats *st) {
             int grid = gate_pass_grid(h->dt, a.k, a.nlow, a.op_end - a.op_begin, threads, h->opt.blocks_per_sm);
             uint64_t ntiles = 1ull << a.nout;
             if ((uint64_t)grid > ntiles) grid = (int)ntiles;
-            {
+            if (a.ph_begin >= 0) {
+                Rec r(h, st, SV_K_GATE, 2.0 * (double)h->state_bytes());
+                const int rg = (int)std::min<uint64_t>(ntiles, (uint64_t)device_sms());
+                SV_CK(launch_gate_reg(h->dt, h->stream, rg, h->psi, a, q->ops.as<DevOp>(), q->phases.as<Phase>(),
+                                      h->coef.p, h->mats.p));
+            } else {
                 Rec r(h, st, SV_K_GATE, 2.0 * (double)h->state_bytes());
                 SV_CK(launch_gate_pass(h->dt, h->stream, grid, threads, h->psi, a, q->ops.as<DevOp>(), h->coef.p,
                                        h->mats.p));
@@ -611,8 +619,12 @@ sv_status run_reverse(sv_handle *h, QsuEntry *q, sv_stats *st) {
                                               c.host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
                     }
             Rec r(h, st, SV_K_ADJ, 4.0 * (double)h->state_bytes());
-            SV_CK(launch_adj_pass(h->dt, h->stream, grid, threads, h->psi, h->lam, a, q->ops.as<DevOp>(), h->coef.p,
-                                  h->mats.p, h->part.as<double>(), nops));
+            if (a.ph_begin >= 0)
+                SV_CK(launch_adj_reg(h->dt, h->stream, grid, h->psi, h->lam, a, q->ops.as<DevOp>(),
+                                     q->phases.as<Phase>(), h->coef.p, h->mats.p, h->part.as<double>(), nops));
+            else
+                SV_CK(launch_adj_pass(h->dt, h->stream, grid, threads, h->psi, h->lam, a, q->ops.as<DevOp>(),
+                                      h->coef.p, h->mats.p, h->part.as<double>(), nops));
             if (st) st->adj_passes++;
         }
         const Tile &T = P.tiles[t];

@@ -409,6 +409,337 @@ __global__ void __launch_bounds__(512) k_adj_pass(Cx<R> *__restrict__ psi, Cx<R>
     }
 }
 
+// ------------------------------------------------- register-blocked passes --
+// A pass of RY / RZ / CZ / 1-qubit matrices runs in phases (host planned):
+// in a phase each of the 512 threads holds the 2^RB amplitudes spanned by
+// the phase's register bits (rmask) of the staged tile, gathered from shared
+// memory; non-diagonal gates act on register bits, diagonal gates on any bit
+// (a thread bit just selects the phase or sign for all of its registers).
+// One shared-memory transpose per phase instead of one barrier per gate.
+__device__ __forceinline__ uint32_t swz_tile(uint32_t i) {
+    return i ^ (((i >> 4) ^ (i >> 8)) & 15u);   // bijection; spreads strided lanes over the banks
+}
+
+template <typename R, int V, int B>
+__device__ __forceinline__ void reg_rot(Cx<R> *x, R c, R s) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (!(v & (1 << B))) rot<R>(x[v], x[v | (1 << B)], c, s);
+}
+template <typename R, int V, int B>
+__device__ __forceinline__ void reg_mat1(Cx<R> *x, const Cx<R> *M, bool adj) {
+    const Cx<R> m00 = mel<R>(M, 2, 0, 0, adj), m01 = mel<R>(M, 2, 0, 1, adj);
+    const Cx<R> m10 = mel<R>(M, 2, 1, 0, adj), m11 = mel<R>(M, 2, 1, 1, adj);
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (!(v & (1 << B))) {
+            const Cx<R> a = x[v], b = x[v | (1 << B)];
+            x[v] = mk<R>(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                         m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x);
+            x[v | (1 << B)] = mk<R>(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                                    m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x);
+        }
+}
+// multiply by (c, s) where bit B of v is 1 and by (c, -s) where it is 0
+template <typename R, int V, int B>
+__device__ __forceinline__ void reg_rz(Cx<R> *x, R c, R s) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const R ss = (v & (1 << B)) ? s : -s;
+        x[v] = mk<R>(c * x[v].x - ss * x[v].y, c * x[v].y + ss * x[v].x);
+    }
+}
+template <typename R, int V, int B0, int B1>
+__device__ __forceinline__ void reg_cz2(Cx<R> *x) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if ((v & (1 << B0)) && (v & (1 << B1))) x[v] = mk<R>(-x[v].x, -x[v].y);
+}
+template <typename R, int V, int B>
+__device__ __forceinline__ void reg_neg_bit(Cx<R> *x) {
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (v & (1 << B)) x[v] = mk<R>(-x[v].x, -x[v].y);
+}
+
+#define SV_REG_SWITCH(b, CALL)                                   \
+    switch (b) {                                                 \
+    case 0: CALL(0); break;                                      \
+    case 1: if constexpr (RB > 1) { CALL(1); } break;            \
+    case 2: if constexpr (RB > 2) { CALL(2); } break;            \
+    case 3: if constexpr (RB > 3) { CALL(3); } break;            \
+    case 4: if constexpr (RB > 4) { CALL(4); } break;            \
+    default: break;                                              \
+    }
+
+// One gate on the registers of a phase.  rmask: register tile bits; base:
+// the thread's tile index bits outside rmask.
+template <typename R, int RB>
+__device__ __forceinline__ void reg_apply(Cx<R> *x, const DevOp &op, uint32_t rmask, uint32_t base, const R *coef,
+                                          const Cx<R> *mats, bool adj) {
+    constexpr int V = 1 << RB;
+    const int t0 = op.t[0];
+    const int b0 = __popc(rmask & ((1u << t0) - 1u));
+    switch (op.kind) {
+    case SV_RY: {
+        const R c = coef[2 * op.gate], s = adj ? -coef[2 * op.gate + 1] : coef[2 * op.gate + 1];
+#define SV_C(B) reg_rot<R, V, B>(x, c, s)
+        SV_REG_SWITCH(b0, SV_C)
+#undef SV_C
+        break;
+    }
+    case SV_MAT1: {
+        const Cx<R> *M = mats + op.mat;
+#define SV_C(B) reg_mat1<R, V, B>(x, M, adj)
+        SV_REG_SWITCH(b0, SV_C)
+#undef SV_C
+        break;
+    }
+    case SV_RZ: {
+        const R c = coef[2 * op.gate], s = adj ? -coef[2 * op.gate + 1] : coef[2 * op.gate + 1];
+        if ((rmask >> t0) & 1u) {
+#define SV_C(B) reg_rz<R, V, B>(x, c, s)
+            SV_REG_SWITCH(b0, SV_C)
+#undef SV_C
+        } else {
+            const R ss = ((base >> t0) & 1u) ? s : -s;
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = mk<R>(c * x[v].x - ss * x[v].y, c * x[v].y + ss * x[v].x);
+        }
+        break;
+    }
+    case SV_CZ: {
+        const int t1 = op.t[1];
+        const bool r0 = (rmask >> t0) & 1u, r1 = (rmask >> t1) & 1u;
+        if (r0 && r1) {
+            const int b1 = __popc(rmask & ((1u << t1) - 1u));
+            const int lo = min(b0, b1), hi = max(b0, b1);
+            switch (lo * 8 + hi) {
+#define SV_CZ_CASE(L, H) case L * 8 + H: if constexpr (RB > H) { reg_cz2<R, V, L, H>(x); } break;
+                SV_CZ_CASE(0, 1) SV_CZ_CASE(0, 2) SV_CZ_CASE(0, 3) SV_CZ_CASE(0, 4)
+                SV_CZ_CASE(1, 2) SV_CZ_CASE(1, 3) SV_CZ_CASE(1, 4)
+                SV_CZ_CASE(2, 3) SV_CZ_CASE(2, 4) SV_CZ_CASE(3, 4)
+#undef SV_CZ_CASE
+            default: break;
+            }
+        } else if (r0 || r1) {
+            const int tr = r0 ? t0 : t1, tt = r0 ? t1 : t0;
+            if ((base >> tt) & 1u) {
+                const int br = __popc(rmask & ((1u << tr) - 1u));
+#define SV_C(B) reg_neg_bit<R, V, B>(x)
+                SV_REG_SWITCH(br, SV_C)
+#undef SV_C
+            }
+        } else if (((base >> t0) & (base >> t1)) & 1u) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = mk<R>(-x[v].x, -x[v].y);
+        }
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// Gradient part Im<lambda|G|psi> of a parametric gate on the registers (G = Y
+// for RY, Z for RZ), then U^dagger on both register sets.
+template <typename R, int V, int B>
+__device__ __forceinline__ R reg_ry_adj(Cx<R> *p, Cx<R> *l, R c, R s) {
+    R g = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+        if (!(v & (1 << B))) {
+            const int w = v | (1 << B);
+            g += (l[w].x * p[v].x + l[w].y * p[v].y) - (l[v].x * p[w].x + l[v].y * p[w].y);
+            rot<R>(p[v], p[w], c, s);
+            rot<R>(l[v], l[w], c, s);
+        }
+    return g;
+}
+template <typename R, int V, int B>
+__device__ __forceinline__ R reg_rz_adj(Cx<R> *p, Cx<R> *l, R c, R s) {
+    R g = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const bool one = v & (1 << B);
+        const R im = l[v].x * p[v].y - l[v].y * p[v].x;
+        g += one ? -im : im;
+        const R ss = one ? s : -s;
+        p[v] = mk<R>(c * p[v].x - ss * p[v].y, c * p[v].y + ss * p[v].x);
+        l[v] = mk<R>(c * l[v].x - ss * l[v].y, c * l[v].y + ss * l[v].x);
+    }
+    return g;
+}
+
+template <typename R, int RB>
+__device__ __forceinline__ R reg_adjoint(Cx<R> *p, Cx<R> *l, const DevOp &op, uint32_t rmask, uint32_t base,
+                                         const R *coef, const Cx<R> *mats) {
+    constexpr int V = 1 << RB;
+    const int t0 = op.t[0];
+    const int b0 = __popc(rmask & ((1u << t0) - 1u));
+    R g = 0;
+    if (op.kind == SV_RY) {
+        const R c = coef[2 * op.gate], s = -coef[2 * op.gate + 1];
+#define SV_C(B) g = reg_ry_adj<R, V, B>(p, l, c, s)
+        SV_REG_SWITCH(b0, SV_C)
+#undef SV_C
+    } else if (op.kind == SV_RZ) {
+        const R c = coef[2 * op.gate], s = -coef[2 * op.gate + 1];
+        if ((rmask >> t0) & 1u) {
+#define SV_C(B) g = reg_rz_adj<R, V, B>(p, l, c, s)
+            SV_REG_SWITCH(b0, SV_C)
+#undef SV_C
+        } else {
+            const bool one = (base >> t0) & 1u;
+            const R ss = one ? s : -s;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const R im = l[v].x * p[v].y - l[v].y * p[v].x;
+                g += one ? -im : im;
+                p[v] = mk<R>(c * p[v].x - ss * p[v].y, c * p[v].y + ss * p[v].x);
+                l[v] = mk<R>(c * l[v].x - ss * l[v].y, c * l[v].y + ss * l[v].x);
+            }
+        }
+    } else {
+        reg_apply<R, RB>(p, op, rmask, base, coef, mats, true);
+        reg_apply<R, RB>(l, op, rmask, base, coef, mats, true);
+    }
+    return g;
+}
+#undef SV_REG_SWITCH
+
+// Thread's tile index bits outside rmask, and the register spread table.
+template <int RB>
+__device__ __forceinline__ void phase_index(uint32_t rmask, int k, uint32_t &base, uint32_t *sp) {
+    const uint32_t tb = ((k >= 32) ? 0xFFFFFFFFu : ((1u << k) - 1u)) & ~rmask;
+    base = 0;
+    uint32_t t = threadIdx.x, m = tb;
+    while (m) {
+        const uint32_t lowbit = m & (0u - m);
+        if (t & 1u) base |= lowbit;
+        t >>= 1;
+        m ^= lowbit;
+    }
+    uint32_t rb[RB];
+    uint32_t rm = rmask;
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+        rb[i] = rm & (0u - rm);
+        rm ^= rb[i];
+    }
+    sp[0] = 0;
+#pragma unroll
+    for (int v = 1; v < (1 << RB); ++v) sp[v] = sp[v & (v - 1)] | rb[__ffs(v) - 1];
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, const GatePassArgs a,
+                                                     const DevOp *__restrict__ ops, const Phase *__restrict__ phases,
+                                                     const R *__restrict__ coef, const Cx<R> *__restrict__ mats) {
+    constexpr int V = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem[];
+    Cx<R> *tile = reinterpret_cast<Cx<R> *>(smem);
+    const uint32_t T = 1u << a.k;
+    const uint32_t nh = 1u << (a.k - a.nlow);
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(tile + T);
+    for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
+    __syncthreads();
+    const uint64_t ntiles = 1ull << a.nout;
+    const uint32_t lowmask = (1u << a.nlow) - 1u;
+    for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const uint64_t gbase = deposit(ti, a.out, a.nout);
+        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) tile[swz_tile(j)] = psi[gbase | hioff[j >> a.nlow] | (j & lowmask)];
+        __syncthreads();
+        for (int ph = a.ph_begin; ph < a.ph_end; ++ph) {
+            const Phase P = phases[ph];
+            uint32_t base, sp[V];
+            phase_index<RB>(P.rmask, a.k, base, sp);
+            Cx<R> x[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
+            for (int o = P.op_begin; o < P.op_end; ++o) {
+                const DevOp op = ops[o];
+                reg_apply<R, RB>(x, op, P.rmask, base, coef, mats, false);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) tile[swz_tile(base | sp[v])] = x[v];
+            __syncthreads();
+        }
+        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = tile[swz_tile(j)];
+        __syncthreads();
+    }
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
+                                                    const GatePassArgs a, const DevOp *__restrict__ ops,
+                                                    const Phase *__restrict__ phases, const R *__restrict__ coef,
+                                                    const Cx<R> *__restrict__ mats, double *__restrict__ part,
+                                                    int part_stride) {
+    constexpr int V = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t T = 1u << a.k;
+    const uint32_t nh = 1u << (a.k - a.nlow);
+    const int nops = a.op_end - a.op_begin;
+    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Cx<R> *tp = reinterpret_cast<Cx<R> *>(smem);
+    Cx<R> *tl = tp + T;
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + T);
+    double *acc = reinterpret_cast<double *>(hioff + nh);
+    for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
+    for (int j = threadIdx.x; j < nops * nwarps; j += blockDim.x) acc[j] = 0.0;
+    __syncthreads();
+    const uint64_t ntiles = 1ull << a.nout;
+    const uint32_t lowmask = (1u << a.nlow) - 1u;
+    for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const uint64_t gbase = deposit(ti, a.out, a.nout);
+        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
+            const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
+            tp[swz_tile(j)] = psi[gi];
+            tl[swz_tile(j)] = lam[gi];
+        }
+        __syncthreads();
+        for (int ph = a.ph_end - 1; ph >= a.ph_begin; --ph) {
+            const Phase P = phases[ph];
+            uint32_t base, sp[V];
+            phase_index<RB>(P.rmask, a.k, base, sp);
+            Cx<R> xp[V], xl[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint32_t si = swz_tile(base | sp[v]);
+                xp[v] = tp[si];
+                xl[v] = tl[si];
+            }
+            for (int o = P.op_end - 1; o >= P.op_begin; --o) {
+                const DevOp op = ops[o];
+                R g = reg_adjoint<R, RB>(xp, xl, op, P.rmask, base, coef, mats);
+                if (has_param(op.kind)) {
+                    g = warp_sum<R>(g);
+                    if (lane == 0) acc[(o - a.op_begin) * nwarps + warp] += (double)g;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const uint32_t si = swz_tile(base | sp[v]);
+                tp[si] = xp[v];
+                tl[si] = xl[v];
+            }
+            __syncthreads();
+        }
+        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
+            const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
+            psi[gi] = tp[swz_tile(j)];
+            lam[gi] = tl[swz_tile(j)];
+        }
+        __syncthreads();
+    }
+    for (int o = threadIdx.x; o < nops; o += blockDim.x) {
+        double tsum = 0.0;
+        for (int w = 0; w < nwarps; ++w) tsum += acc[o * nwarps + w];
+        part[(size_t)blockIdx.x * part_stride + a.op_begin + o] = tsum;
+    }
+}
+
 // -------------------------------------------------------------------- K-QR --
 struct SwapArgs {
     int n, L, ntb, nlo, nhi, nout;
@@ -614,6 +945,97 @@ __device__ __forceinline__ uint32_t pair_select(const ThreadCoset &tc, uint32_t 
     return all & (((tc.l >> pl) & 1u) ? ph : ~ph);
 }
 
+// The same split as (h, s): take the elements j whose bit h equals s, or
+// every element (h = -1, factor 1).
+struct PairSel {
+    int h, s, fac;
+};
+
+__device__ __forceinline__ PairSel pair_split(const ThreadCoset &tc, uint32_t X, int kl, int ept) {
+    const int jb = __ffs(ept) - 1;
+    const uint32_t c = X >> kl;
+    if (c) {
+        const int cb = __ffs(c) - 1;
+        if (cb >= (int)tc.ash) return {cb - (int)tc.ash, 0, 2};
+        const uint32_t cj = c >> tc.ash;
+        for (int h = 0; h < jb; ++h)
+            if (!((cj >> h) & 1u)) return {h, (int)((tc.a0 >> cb) & 1u), 2};
+        return {-1, 0, 1};
+    }
+    if (jb == 0) return {-1, 0, 1};
+    return {0, (int)((tc.l >> (__ffs(X) - 1)) & 1u), 2};
+}
+
+// val with its sign flipped when bit j of sm is set.
+template <int J>
+__device__ __forceinline__ float flip_bit(float v, uint32_t sm) {
+    return __int_as_float(__float_as_int(v) ^ (int)((sm << (31 - J)) & 0x80000000u));
+}
+template <int J>
+__device__ __forceinline__ double flip_bit(double v, uint32_t sm) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)((sm >> J) & 1u) << 63));
+}
+
+// Sum over the selected elements j = (j' with bit S inserted at H) of the
+// pair term Re or Im(conj(partner) own), signed by sm.  NT = 512, E = EPT*NT.
+template <typename R, int EPT, int H, int S, bool ODD>
+__device__ __forceinline__ R evc_sel_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
+    R a0 = 0, a1 = 0;
+    const uint32_t xl = X & 511u, xh = X >> 9;
+    const Cx<R> *tb = t + (threadIdx.x ^ xl);
+#pragma unroll
+    for (int jp = 0; jp < EPT / 2; ++jp) {
+        constexpr int dummy = 0;
+        (void)dummy;
+        const int j = ((jp >> H) << (H + 1)) | (S << H) | (jp & ((1 << H) - 1));
+        const Cx<R> u = own[j];
+        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
+        const R val = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
+        R f;
+        switch (j) {   // compile-time after unrolling
+#define SV_FB(J) case J: f = flip_bit<J>(val, sm); break;
+            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
+            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
+#undef SV_FB
+        default: f = val; break;
+        }
+        if (jp & 1) a1 += f; else a0 += f;
+    }
+    return a0 + a1;
+}
+
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ R evc_all_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
+    R a0 = 0, a1 = 0;
+    const uint32_t xl = X & 511u, xh = X >> 9;
+    const Cx<R> *tb = t + (threadIdx.x ^ xl);
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const Cx<R> u = own[j];
+        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
+        const R val = X ? (ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y)) : (u.x * u.x + u.y * u.y);
+        const R f = ((sm >> j) & 1u) ? -val : val;
+        if (j & 1) a1 += f; else a0 += f;
+    }
+    return a0 + a1;
+}
+
+// Fast path (NT = 512, E = EPT * 512): dispatch on (h, s, odd).
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t X, PairSel ps, uint32_t sm) {
+    if (ps.h < 0) return evc_all_loop<R, EPT, ODD>(t, own, X, sm);
+#define SV_SEL(HH)                                                                                       \
+    if (ps.h == HH) {                                                                                    \
+        if constexpr ((1 << (HH + 1)) <= EPT) {                                                          \
+            return ps.s ? evc_sel_loop<R, EPT, HH, 1, ODD>(t, own, X, sm)                                \
+                        : evc_sel_loop<R, EPT, HH, 0, ODD>(t, own, X, sm);                               \
+        }                                                                                                \
+    }
+    SV_SEL(0) SV_SEL(1) SV_SEL(2) SV_SEL(3)
+#undef SV_SEL
+    return (R)0;
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                      const DevGroup *__restrict__ groups,
@@ -758,7 +1180,11 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
         const uint32_t sel = G.X ? pair_select(tc, G.X, a.kl, EPT, fac) : 0xFFFFu;
         const int neg0 = G.X ? ((S.nY == 1) | (S.nY == 2)) : 0;
         const int tconst = (__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ neg0) & 1;
-        pg[g * NT + threadIdx.x] = (sel & 0x7FFFFFFFu) | ((uint32_t)tconst << 31);
+        const PairSel ps = G.X ? pair_split(tc, G.X, a.kl, EPT) : PairSel{-1, 0, 1};
+        // packed: sel (bits 0..15), split bit h + 1 (bits 16..19, 0 = every element),
+        // side s (bit 20), sign constant (bit 31)
+        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | ((uint32_t)(ps.h + 1) << 16) | ((uint32_t)ps.s << 20) |
+                                   ((uint32_t)tconst << 31);
         acc32[g * NT + threadIdx.x] = (R)0;
         if (threadIdx.x == 0) {
             gz[g] = S.z;
@@ -773,6 +1199,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
     for (int g = 0; g < kEvcFew; ++g) d[g] = 0.0;
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const bool fast = (NT == 512) && (E == (uint32_t)EPT * 512u) && EPT >= 2;
     for (uint64_t k = 0; k < 2; ++k) {
         if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
         cp_async_commit();
@@ -794,9 +1221,13 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
             const uint32_t X = gX[g];
             const int meta = gmeta[g];
             const int base = ((int)(p >> 31) ^ __popcll(rep & gz[g])) & 1;
-            const uint32_t sel = X ? (p & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+            const uint32_t sel = X ? (p & 0xFFFFu) : 0xFFFFFFFFu;
             R v;
-            if (X == 0u) {
+            if (fast) {
+                const uint32_t sm = base ? ~gjm[g] : gjm[g];
+                const PairSel ps{(int)((p >> 16) & 15u) - 1, (int)((p >> 20) & 1u), 0};
+                v = (meta & 1) ? evc_fast<R, EPT, true>(t, own, X, ps, sm) : evc_fast<R, EPT, false>(t, own, X, ps, sm);
+            } else if (X == 0u) {
                 v = 0;
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
@@ -868,6 +1299,33 @@ __device__ __forceinline__ void hpsi_one(Cx<R> *acc, const Cx<R> *t, uint32_t X,
     }
 }
 
+// Fast path of hpsi_one (NT = 512, E = EPT * 512): compile-time element
+// offsets, the sign as a bit flip of the coefficient.
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ void hpsi_fast(Cx<R> *acc, const Cx<R> *t, uint32_t X, uint32_t sm, R g) {
+    const uint32_t xl = X & 511u, xh = X >> 9;
+    const Cx<R> *tb = t + (threadIdx.x ^ xl);
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
+        R f;
+        switch (j) {
+#define SV_FB(J) case J: f = flip_bit<J>(g, sm); break;
+            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
+            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
+#undef SV_FB
+        default: f = g; break;
+        }
+        if (ODD) {
+            acc[j].x -= f * v.y;
+            acc[j].y += f * v.x;
+        } else {
+            acc[j].x += f * v.x;
+            acc[j].y += f * v.y;
+        }
+    }
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
                                                       const CosetArgs a, const DevGroup *__restrict__ groups,
@@ -884,6 +1342,7 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
     const uint32_t lowmask = (1u << a.kl) - 1u;
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const bool fast = (blockDim.x == 512) && (E == (uint32_t)EPT * 512u);
     for (uint64_t k = 0; k < 2; ++k) {
         if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
         cp_async_commit();
@@ -910,8 +1369,15 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
                 const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
                 const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                 const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
-                if (S.nY & 1) hpsi_one<R, EPT, true>(acc, t, G.X, base, jm, g, E);
-                else hpsi_one<R, EPT, false>(acc, t, G.X, base, jm, g, E);
+                if (fast) {
+                    const uint32_t sm = base ? ~jm : jm;
+                    if (S.nY & 1) hpsi_fast<R, EPT, true>(acc, t, G.X, sm, g);
+                    else hpsi_fast<R, EPT, false>(acc, t, G.X, sm, g);
+                } else if (S.nY & 1) {
+                    hpsi_one<R, EPT, true>(acc, t, G.X, base, jm, g, E);
+                } else {
+                    hpsi_one<R, EPT, false>(acc, t, G.X, base, jm, g, E);
+                }
             }
         }
         R eloc = 0;
@@ -1282,6 +1748,59 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
                                                        (const double2 *)mats);
     }
     return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePassArgs &a, const DevOp *ops,
+                              const Phase *phases, const void *coef, const void *mats) {
+    const size_t sm = ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 + 64;
+    switch (a.k - 9) {
+#define SV_GR(RB)                                                                                            \
+    case RB:                                                                                                 \
+        allow_smem(k_gate_reg<R, RB>, sm);                                                                   \
+        k_gate_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, a, ops, phases, (const R *)coef,              \
+                                                 (const Cx<R> *)mats);                                       \
+        break;
+        SV_GR(2) SV_GR(3) SV_GR(4)
+#undef SV_GR
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
+                             const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
+                             int part_stride) {
+    const size_t sm = 2 * ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
+                      (size_t)(a.op_end - a.op_begin) * 16 * 8 + 64;
+    switch (a.k - 9) {
+#define SV_AR(RB)                                                                                            \
+    case RB:                                                                                                 \
+        allow_smem(k_adj_reg<R, RB>, sm);                                                                    \
+        k_adj_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases, (const R *)coef, \
+                                                (const Cx<R> *)mats, part, part_stride);                     \
+        break;
+        SV_AR(2) SV_AR(3) SV_AR(4)
+#undef SV_AR
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gate_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, const GatePassArgs &a,
+                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats) {
+    if (dt == SV_C64) return gate_reg_dispatch<float>(st, grid, psi, a, ops, phases, coef, mats);
+    return gate_reg_dispatch<double>(st, grid, psi, a, ops, phases, coef, mats);
+}
+
+cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
+                           const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
+                           int part_stride) {
+    if (dt == SV_C64) return adj_reg_dispatch<float>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride);
+    return adj_reg_dispatch<double>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride);
 }
 
 cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi, void *lam,

@@ -13,6 +13,7 @@ namespace sv {
 // physical bits that are not staged (they index the tiles).
 struct GatePassArgs {
     int n, k, nlow, nhi, nout, op_begin, op_end;
+    int ph_begin, ph_end;    // register phases (register-blocked pass), else -1
     int8_t hi[40];
     int8_t out[64];
 };
@@ -77,6 +78,12 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
 cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi, void *lam,
                             const GatePassArgs &a, const DevOp *ops, const void *coef, const void *mats,
                             double *part, int part_stride);
+// Register-blocked passes (512 threads; a.ph_begin >= 0, 11 <= k <= 13).
+cudaError_t launch_gate_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, const GatePassArgs &a,
+                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats);
+cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
+                           const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
+                           int part_stride);
 // In-place swap of disjoint physical bit pairs (pairs[2i], pairs[2i+1]).
 cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const int32_t *pairs,
                            int npairs, int blocks_per_sm);

@@ -287,6 +287,72 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low) {
     }
 }
 
+// ------------------------------------------------------- register phases --
+// A pass made only of RY, RZ, CZ and 1-qubit matrices is run register
+// blocked: every thread holds 2^r amplitudes spanned by r tile bits (the
+// register set).  Non-diagonal gates need their target in the register set;
+// diagonal gates (RZ, CZ) apply in any layout.  Phases are built like the
+// tiles: the register set takes the targets of the earliest remaining
+// non-diagonal gates (padded with the lowest free tile bits), then the phase
+// takes gates in order while they fit, a gate that does not fit blocking its
+// targets (C1 is kept).  The pass's ops are reordered phase by phase.
+bool diag_kind(int kind) { return kind == SV_RZ || kind == SV_CZ; }
+
+void plan_phases(QsuPlan &P) {
+    for (auto &gp : P.passes) {
+        const int r = gp.k - 9;                       // 512 threads
+        if (r < 2) continue;
+        bool ok = true;
+        for (int o = gp.op_begin; o < gp.op_end; ++o) {
+            const int kd = P.ops[o].kind;
+            if (kd != SV_RY && kd != SV_RZ && kd != SV_CZ && kd != SV_MAT1) ok = false;
+        }
+        if (!ok) continue;
+        const uint32_t all = (gp.k >= 32) ? 0xFFFFFFFFu : ((1u << gp.k) - 1u);
+        auto tmask = [&](const DevOp &d) {
+            uint32_t m = 0;
+            const int nq = (d.kind == SV_CZ) ? 2 : 1;
+            for (int i = 0; i < nq; ++i) m |= 1u << d.t[i];
+            return m;
+        };
+        std::vector<DevOp> remain(P.ops.begin() + gp.op_begin, P.ops.begin() + gp.op_end), next, out;
+        gp.ph_begin = (int32_t)P.phases.size();
+        while (!remain.empty()) {
+            uint32_t Rm = 0, avail = all;
+            for (auto &d : remain) {
+                const uint32_t t = tmask(d);
+                if (diag_kind(d.kind)) {
+                    if (t & ~avail) avail &= ~t;
+                    continue;
+                }
+                if ((t & ~avail) == 0 && __builtin_popcount(Rm | t) <= r) Rm |= t;
+                else avail &= ~t;
+                if (!avail || __builtin_popcount(Rm) == r) break;
+            }
+            for (uint32_t fr = all & ~Rm; __builtin_popcount(Rm) < r && fr; fr &= fr - 1) Rm |= fr & (0u - fr);
+            Phase ph;
+            ph.rmask = Rm;
+            ph.op_begin = gp.op_begin + (int32_t)out.size();
+            uint32_t av = all;
+            next.clear();
+            for (auto &d : remain) {
+                const uint32_t t = tmask(d);
+                const bool fits = (t & ~av) == 0 && (diag_kind(d.kind) || (t & ~Rm) == 0);
+                if (fits) out.push_back(d);
+                else {
+                    av &= ~t;
+                    next.push_back(d);
+                }
+            }
+            ph.op_end = gp.op_begin + (int32_t)out.size();
+            P.phases.push_back(ph);
+            remain.swap(next);
+        }
+        gp.ph_end = (int32_t)P.phases.size();
+        std::copy(out.begin(), out.end(), P.ops.begin() + gp.op_begin);
+    }
+}
+
 // ---------------------------------------------------------- coset passes --
 // Strings sharing a physical X/Y mask x form a group: one read of psi serves
 // all of them.  A pass stages 2^(kl+m) amplitudes: the 2^m runs of 2^kl
@@ -658,6 +724,7 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
     if (P.tiles.empty()) P.final_l2p = l2p_init;
     int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
     plan_gate_passes(P, ops, k, o.low_bits);
+    plan_phases(P);
     return "";
 }
 

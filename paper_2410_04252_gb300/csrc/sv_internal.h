@@ -48,7 +48,18 @@ struct GatePass {
     int32_t k = 0, nlow = 0;          // staged bits, of which the nlow lowest are contiguous
     uint64_t bits = 0;                // physical staged bits
     int32_t op_begin = 0, op_end = 0; // into QsuPlan::ops
+    int32_t ph_begin = -1, ph_end = -1;  // register phases (register-blocked passes), else -1
 };
+
+// A register phase of a register-blocked pass: each thread holds the
+// amplitudes spanned by the tile bits in rmask; ops [op_begin, op_end) are
+// applied in registers (non-diagonal gates on rmask bits, diagonal gates on
+// any bits).
+struct Phase {
+    uint32_t rmask;
+    int32_t op_begin, op_end;
+};
+constexpr int kRegThreads = 512;      // CTA size of register-blocked passes (r = k - 9)
 
 struct QsuPlan {
     int n = 0, g = 0, nL = 0;
@@ -56,6 +67,7 @@ struct QsuPlan {
     std::vector<Tile> tiles;
     std::vector<GatePass> passes;
     std::vector<DevOp> ops;           // pass operations, pass by pass, in execution order
+    std::vector<Phase> phases;        // register phases of register-blocked passes
     std::vector<int32_t> init_l2p, final_l2p;
     int32_t nqr() const {
         int32_t c = 0;
