@@ -33,6 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "VQE iter time (QSU+EVC+adjoint grad), HBM GB/s vs peak; lazy-QR vs eager"
+BATCH_METRIC = "batched VQE iterations (QSU+EVC+adjoint grad), per-state latency and throughput"
 
 
 def parse():
@@ -47,6 +48,9 @@ def parse():
     ap.add_argument("--eager-warmup", type=int, default=1)
     ap.add_argument("--no-eager", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-direct", action="store_true")
+    ap.add_argument("--plan-table", action="store_true", help="print plan-level QR counts (host only) and exit")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: default options")
     ap.add_argument("--cpu-n", type=int, default=22, help="oracle sample size (qubits)")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--low-bits", type=int, default=0)
@@ -149,33 +153,42 @@ def ncu_traffic(kind: str, launches_bytes: float):
 # ----------------------------------------------------------------- oracle --
 
 def oracle_sample(cfg_id: int, n_full: int, n_s: int, nterm_sample: int = 16):
-    """Time the oracle on a bounded sample and scale it to one full VQE
-    iteration of the oracle: E and the parameter-shift / finite-difference
-    gradient (1 + 2 * np evaluations of QSU + EVC), each evaluation scaled
-    by 2^(n_full - n_s) and by nterms / nterm_sample for the EVC."""
+    """Time the oracle on a bounded sample and scale it to one full step of
+    the workload computed the oracle's way: QSU (gate by gate), EVC (string by
+    string) and, for the gradient workload, the parameter-shift gradient
+    (1 + 2 * np evaluations of QSU + EVC); each evaluation scaled by
+    2^(n_full - n_s), by the gate count and by nterms / nterm_sample."""
     import numpy as np
     import oracle
     from paper_2410_04252_gb300 import workloads as W
     cfg = W.CONFIGS[cfg_id]
-    circ = W.make_circuit(cfg, n_s)
+    batch = cfg.get("batch", 1)
+    # batched workload: one state of the mean depth stands for each state
+    layers = (cfg["layers"] + cfg["min_layers"]) // 2 if batch > 1 else cfg["layers"]
+    circ = W.make_circuit(cfg, n_s, layers)
     params = W.make_params(cfg_id, circ)
     ham = W.make_hamiltonian(cfg_id, n_s)
-    sub = W.Hamiltonian(n_s, ham.letters[:nterm_sample], ham.coeffs[:nterm_sample])
     init = W.make_init(cfg, n_s)
     t0 = time.perf_counter()
     psi = oracle.apply_circuit(oracle.basis_state(n_s, init), circ, params)
     t1 = time.perf_counter()
-    oracle.energy(psi, sub)
+    if ham is not None:
+        sub = W.Hamiltonian(n_s, ham.letters[:nterm_sample], ham.coeffs[:nterm_sample])
+        oracle.energy(psi, sub)
     t2 = time.perf_counter()
-    full_circ = W.make_circuit(cfg, n_full)
+    full_circ = W.make_circuit(cfg, n_full, layers)
     scale = 2.0 ** (n_full - n_s)
     t_qsu = (t1 - t0) * scale * full_circ.m / max(circ.m, 1)
-    t_evc = (t2 - t1) * scale * cfg["nterms"] / nterm_sample * (n_full / n_s)
-    evals = 1 + 2 * full_circ.nparams
-    est_ms = (t_qsu + t_evc) * evals * 1e3
-    sample = (f"oracle FP64 QSU of the same ansatz at n={n_s} ({circ.m} gates) + EVC of {nterm_sample} "
-              f"of the {cfg['nterms']} strings, {t2 - t0:.2f} s; scaled by 2^{n_full - n_s}, gate count, "
-              f"string count and {evals} evaluations (energy + parameter-shift gradient)")
+    t_evc = (t2 - t1) * scale * cfg["nterms"] / nterm_sample * (n_full / n_s) if ham is not None else 0.0
+    evals = 1 + 2 * full_circ.nparams if cfg["work"] in ("qsu+evc+grad", "batch") else 1
+    est_ms = (t_qsu + t_evc) * evals * batch * 1e3
+    what = {"qsu": "", "qsu+evc": "", "qsu+evc+grad": " and %d evaluations (energy + parameter-shift gradient)" % evals,
+            "batch": " and %d evaluations (energy + parameter-shift gradient) per state, %d states of %d layers"
+                     % (evals, batch, layers)}
+    sample = (f"oracle FP64 QSU of the same ansatz at n={n_s} ({circ.m} gates)"
+              + (f" + EVC of {nterm_sample} of the {cfg['nterms']} strings" if ham is not None else "")
+              + f", {t2 - t0:.2f} s; scaled by 2^{n_full - n_s}, gate count"
+              + (", string count" if ham is not None else "") + what[cfg["work"]])
     return est_ms, sample, t2 - t0
 
 
@@ -201,14 +214,18 @@ def run_reference(args):
         est, sample, w = oracle_sample(args.config, n_full, n_s)
         vals.append(est)
         wall.append(w)
-    value = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+    ms = statistics.median(vals)
+    metric, value, unit, hib = METRIC, ms, "ms", False
+    if cfg["work"] == "batch":
+        metric = BATCH_METRIC
+        value, unit, hib = cfg["batch"] / (ms * 1e-3), "states/s", True
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg["name"], "n": n_full, "g": cfg["g"], "nterms": cfg["nterms"]},
-            "cpu_baseline": {"value": value, "unit": "ms", "cores": omp_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": omp_threads(), "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sample_wall_s": statistics.median(wall)}
     print(json.dumps(line), flush=True)
     return 0
@@ -235,7 +252,7 @@ def run_ours(args):
     circ = W.make_circuit(cfg, n)
     params = W.make_params(args.config, circ)
     ham = W.make_hamiltonian(args.config, n)
-    paulis, coeffs = sv.hamiltonian_arrays(ham)
+    paulis, coeffs = sv.hamiltonian_arrays(ham) if ham is not None else (None, np.zeros(0))
     init = W.make_init(cfg, n)
     opt = sv.default_options(dtype)
     if args.tile_bits:
@@ -255,12 +272,28 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
+    work = cfg["work"]
+
     def step(schedule):
-        return sim.vqe_step(init, circ, params, paulis=paulis, coeffs=coeffs, schedule=schedule)
+        """One step of the workload's path; stats of all its calls merged
+        into sim.last_stats.  Returns (energy, gradient)."""
+        if work == "qsu+evc+grad":
+            e, gr, _ = sim.vqe_step(init, circ, params, paulis=paulis, coeffs=coeffs, schedule=schedule)
+            return e, gr
+        sim.reset(init)
+        st = sim.apply_circuit(circ, params, schedule)
+        e = 0.0
+        if work == "qsu+evc":
+            e, _ = sim.expect(paulis=paulis, coeffs=coeffs, schedule=schedule)
+            st = sv.merge_stats(st, sim.last_stats)
+        else:
+            sim.synchronize()
+        sim.last_stats = st
+        return e, np.zeros(0)
 
     t_setup = time.perf_counter()
     for _ in range(args.warmup):
-        e, gr, _ = step(sv.LAZY)
+        e, gr = step(sv.LAZY)
     plan_s = time.perf_counter() - t_setup
 
     clocks = ClockSampler(local)
@@ -275,7 +308,7 @@ def run_ours(args):
     launches = 0
     counts = {}
     for _ in range(args.steps):
-        e, gr, _ = step(sv.LAZY)
+        e, gr = step(sv.LAZY)
         st = sim.last_stats
         launches += st.launches
         for i, k in enumerate(sv.KERNEL_KINDS):
@@ -310,7 +343,7 @@ def run_ours(args):
         a0.record(stream)
         est = None
         for _ in range(args.eager_steps):
-            ee, eg, _ = step(sv.EAGER)
+            ee, eg = step(sv.EAGER)
             est = sim.last_stats
         a1.record(stream)
         a1.synchronize()
@@ -318,7 +351,24 @@ def run_ours(args):
         eager = {"ms_per_step": eager_ms, "speedup_lazy_over_eager": eager_ms / ms_per_step,
                  "qsu_qrs": est.qsu_qrs, "evc_qrs": est.evc_qrs, "qsu_passes": est.qsu_passes,
                  "evc_passes": est.evc_passes, "steps": args.eager_steps, "warmup": args.eager_warmup,
-                 "energy_diff_vs_lazy": abs(ee - e), "grad_maxdiff_vs_lazy": float(np.max(np.abs(eg - gr)))}
+                 "energy_diff_vs_lazy": abs(ee - e),
+                 "grad_maxdiff_vs_lazy": float(np.max(np.abs(eg - gr))) if gr.size else None}
+
+    # no virtual-chunk constraint (not the paper's method): the single-GPU optimum
+    direct = None
+    if not args.no_direct:
+        step(sv.DIRECT)
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        de, dg = step(sv.DIRECT)
+        dst = sim.last_stats
+        d1.record(stream)
+        d1.synchronize()
+        dms = d0.elapsed_time(d1)
+        direct = {"ms_per_step": dms, "lazy_over_direct": ms_per_step / dms, "qsu_qrs": dst.qsu_qrs,
+                  "evc_qrs": dst.evc_qrs, "evc_passes": dst.evc_passes, "energy_diff_vs_lazy": abs(de - e)}
 
     if rank != 0:
         if dist is not None:
@@ -362,12 +412,17 @@ def run_ours(args):
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "how": "wall clock around the public vqe_step call (host params/Hamiltonian in, energy+grad out)"},
+                "how": {"qsu+evc+grad": "wall clock around the public vqe_step call (host params/Hamiltonian in, "
+                               "energy+grad out)",
+                        "qsu+evc": "wall clock around reset + apply_circuit + expect (host params/Hamiltonian "
+                                   "in, energy out)",
+                        "qsu": "wall clock around reset + apply_circuit + synchronize (host params in)"}[work]},
         "gpu_launches": launches,
         "clocks": clk,
         "kernels": kinds,
         "counts": counts,
         "eager": eager,
+        "direct": direct,
         "energy": e,
         "plan_and_warmup_s": plan_s,
     }
@@ -396,27 +451,55 @@ def run_batch(args):
     params = [p for _, p in states]
     ham = W.make_hamiltonian(4, n)
     paulis, coeffs = sv.hamiltonian_arrays(ham)
+    opt = sv.default_options(sv.C64)
+    tuned_ms = None
+    if not args.no_autotune:
+        # tile size k, CTA size and fusion depth picked by the autotuner
+        opt, tuned_ms = sv.batch_autotune(n, sv.C64, circs, params, paulis=paulis, coeffs=coeffs, reps=2)
     for _ in range(args.warmup):
-        sv.batch_run(n, sv.C64, circs, params, paulis=paulis, coeffs=coeffs)
+        sv.batch_run(n, sv.C64, circs, params, paulis=paulis, coeffs=coeffs, options=opt)
     clocks = ClockSampler(local)
     clocks.start()
     dev_ms, lat = [], []
     w0 = time.perf_counter()
     for _ in range(args.steps):
-        e, g, t, st = sv.batch_run(n, sv.C64, circs, params, paulis=paulis, coeffs=coeffs)
+        e, g, t, st = sv.batch_run(n, sv.C64, circs, params, paulis=paulis, coeffs=coeffs, options=opt)
         dev_ms.append(st.ms[sv.K_BATCH])
         lat.extend(((t[:, 1] - t[:, 0]) * 1e-6).tolist())
     wall_ms = (time.perf_counter() - w0) * 1e3 / args.steps
     clk = clocks.stop()
     ms = statistics.median(dev_ms)
     lat.sort()
+    # algorithmic HBM bytes of one batched launch: per state 2S per gate pass
+    # (QSU), 2S + 3S per later H|psi> pass, 4S per adjoint pass (S = 2^n * 8)
+    S = float(1 << n) * 8
+    npass = {}
+    for c in circs:
+        if c.m not in npass:
+            npass[c.m] = sv.plan_qsu(n, 0, c, sv.LAZY, opt)["npasses"]
+    hp = st.hpsi_passes
+    byts = sum(6 * S * npass[c.m] for c in circs) + len(circs) * S * (2 + 3 * max(hp - 1, 0))
+    peak, peak_src = measured_peaks()
+    achieved = byts / (ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu:
+        est_ms, sample, _ = oracle_sample(4, n, min(args.cpu_n, 14))
+        cpu = {"value": cfg["batch"] / (est_ms * 1e-3), "unit": "states/s", "cores": omp_threads(),
+               "kind": "oracle", "sample": sample}
     line = {
-        "metric": "batched VQE iterations (QSU+EVC+adjoint grad), per-state latency and throughput",
+        "metric": BATCH_METRIC,
         "value": cfg["batch"] / (ms * 1e-3), "unit": "states/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 (f32 math, f64 accumulation)", "data": "synthetic",
         "config": {"workload": cfg["name"], "n": n, "states": cfg["batch"], "layers": "2..8",
-                   "nterms": len(coeffs), "launches_per_step": st.launches, "graph_captured": True},
+                   "nterms": len(coeffs), "launches_per_step": st.launches, "graph_captured": True,
+                   "l2": "inputs larger than L2: psi and lambda per resident CTA, %d SMs x 2 x %.0f MiB" % (
+                       torch.cuda.get_device_properties(local).multi_processor_count, S / 2**20),
+                   "tile_bits": opt.tile_bits, "threads": opt.threads, "fuse_max": opt.fuse_max,
+                   "autotuned": tuned_ms is not None},
+        "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": None},
+        "cpu_baseline": cpu,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "max": lat[-1]},
         "e2e": {"value": cfg["batch"] / (wall_ms * 1e-3), "unit": "states/s",
@@ -430,8 +513,42 @@ def run_batch(args):
     return 0
 
 
+def plan_table(args):
+    """Plan-level QR counts of the QSU experiment (Sec. V-B-1): GateFabric
+    circuits (4-qubit blocks as one operation, and split into the double
+    excitation and two Givens rotations), n = 20..36, 4n layers, 32 chunks
+    (g = 5), flat vs hierarchical (8 chunks per node: 3 intra qubits) vs the
+    ad hoc rule; host planning only, with its time."""
+    from paper_2410_04252_gb300 import sv
+    from paper_2410_04252_gb300 import workloads as W
+    g, nintra = 5, 3
+    rows = []
+    for n in range(20, 37, 2):
+        for form, make in (("blocks", W.fabric_blocks_circuit), ("split", W.fabric_circuit)):
+            c = make(n, 4 * n)
+            hopt = sv.default_options()
+            hopt.intra_bits = nintra
+            row = {"n": n, "form": form, "ops": c.m}
+            for name, sched, opt in (("flat", sv.LAZY, None), ("hier", sv.HIER, hopt), ("adhoc", sv.EAGER, None)):
+                t0 = time.perf_counter()
+                p = sv.plan_qsu(n, g, c, sched, opt)
+                row[name + "_plan_s"] = time.perf_counter() - t0
+                row[name + "_qrs"] = sum(1 for t in p["tiles"] if t["pairs"])
+                if name == "hier":
+                    inter = [(t["local_mask"] | t["intra_mask"]) for t in p["tiles"]]
+                    row["hier_inter_qrs"] = sum(1 for i in range(1, len(inter))
+                                                if inter[i] != inter[i - 1] and p["tiles"][i]["pairs"])
+            row["adhoc_over_flat"] = row["adhoc_qrs"] / max(row["flat_qrs"], 1)
+            rows.append(row)
+    print(json.dumps({"table": "QSU QR counts, flat vs hierarchical vs ad hoc (plan level)", "g": g,
+                      "n_intra": nintra, "layers": "4n", "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.plan_table:
+        return plan_table(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.config == 4:

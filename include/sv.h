@@ -46,8 +46,20 @@ typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
 
 /* Schedules: EAGER = the ad hoc rule (depth order; before each wide operation
  * a QR for that operation alone, Sec. V-B-1); LAZY = time-space tiling
- * (Alg. 1-3 for QSU, Alg. 6 with diagonalization for EVC). */
-typedef enum { SV_SCHED_EAGER = 0, SV_SCHED_LAZY = 1 } sv_schedule;
+ * (Alg. 1-3 for QSU, Alg. 6 with diagonalization for EVC).  DIRECT is not
+ * the paper's method: it drops the virtual-chunk constraint (every qubit is
+ * local, as it may be when the whole state sits in one GPU's memory), so a
+ * plan has one tile and no QR -- gate passes and coset passes may pair
+ * amplitudes of different chunks.  It is the single-GPU optimum the two
+ * schedules are compared against. */
+typedef enum { SV_SCHED_EAGER = 0, SV_SCHED_LAZY = 1, SV_SCHED_DIRECT = 2, SV_SCHED_HIER = 3 } sv_schedule;
+/* SV_SCHED_HIER: QSU by hierarchical tiling (Alg. 4 with Alg. 5) for a
+ * two-layered interconnect whose intra-node part holds options.intra_bits of
+ * the g global qubits (Q_intra starts at physical positions n-g ..
+ * n-g+intra_bits-1); the remapping prefers an intra QR (next local set drawn
+ * from Q_L u Q_intra) over an inter QR.  On one GPU every QR is the same
+ * in-place permutation; the plan export tells intra from inter QRs
+ * (sv_plan_tile_intra).  EVC under SV_SCHED_HIER is the LAZY one (Alg. 6). */
 
 enum { SV_RY = 0, SV_RZ = 1, SV_CZ = 2, SV_GIVENS = 3, SV_DEXC = 4,
        SV_MAT1 = 5, SV_MAT2 = 6, SV_MAT4 = 7 };
@@ -76,7 +88,7 @@ typedef struct {
     int32_t evc_low_bits;       /* shortest contiguous run (bits) of an EVC / H|psi> coset pass (default 5 c64,
                                    4 c128); a pass stages 2^(evc_low_bits + evc_span) amplitudes and lengthens
                                    its runs when it needs a smaller span */
-    int32_t evc_span;           /* max coset dimension m of an EVC / H|psi> pass (default 8) */
+    int32_t evc_span;           /* max coset dimension m of an EVC / H|psi> pass (default 8, at most 10) */
     int32_t pad_highest;        /* Alg. 3 padding: 1 highest free qubit (default), 0 lowest (printed text) */
     int32_t checkpoint_every;   /* c > 0: the forward sweep keeps a copy of psi after every c-th gate pass
                                    (device memory, else pinned host memory) and the adjoint sweep
@@ -86,6 +98,9 @@ typedef struct {
     int64_t wait_limit;         /* spin iterations before a device wait gives up (batched kernel) */
     int32_t profile;            /* 1: time every launch with CUDA events on the stream (sv_stats.ms);
                                    calls then synchronise before returning */
+    int32_t fuse_max;           /* fusion depth: at most this many gate operations per gate pass
+                                   (0 = as many as fit, up to 256) */
+    int32_t intra_bits;         /* SV_SCHED_HIER: intra-node global qubits n_intra, 0 <= n_intra <= g */
     int32_t reserved;
 } sv_options;
 
@@ -252,6 +267,10 @@ sv_status sv_plan_tile(const sv_plan *p, int32_t t, int32_t *begin, int32_t *end
  * operation indices it applies, in order (ops may be NULL to query nops). */
 sv_status sv_plan_pass(const sv_plan *p, int32_t i, int32_t *tile, uint64_t *bits,
                        int32_t *nops, int32_t *ops);
+/* Hierarchical plans: the logical intra set Q_intra in force during tile t
+ * (0 for other schedules).  A QR before tile t is an inter QR when the inter
+ * set Q \ (Q_L u Q_intra) differs from the previous tile's (Fig. 7). */
+sv_status sv_plan_tile_intra(const sv_plan *p, int32_t t, uint64_t *intra_mask);
 void sv_plan_free(sv_plan *p);
 
 /*
@@ -296,6 +315,40 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch,
 sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, const sv_pauli *paulis,
                             const double *coeffs, size_t nterms, double *energy, double *per_term,
                             void *stream);
+
+/*
+ * Autotuner (the paper fixes neither the pass size nor the fusion depth: both
+ * are parameters of this implementation).  Picks tile_bits (k), fuse_max
+ * (fusion depth) and, when nterms > 0, the coset pass shape (evc_low_bits,
+ * evc_span) for this handle by timing one step per candidate, coordinate by
+ * coordinate from the handle's current options.  The step is sv_vqe_step
+ * when nterms > 0, else sv_reset_basis + sv_apply_circuit.  Each candidate
+ * runs once untimed (planning) and reps >= 1 times timed (host wall clock
+ * around synchronised calls; the minimum counts).  The fastest options are
+ * left set on the handle and copied to *best (nullable); *best_ms (nullable)
+ * receives their time.  Overwrites the state.  Synchronises.
+ */
+sv_status sv_autotune(sv_handle *h, uint64_t init_index, const sv_gate *gates, size_t m,
+                      const double *params, size_t np, const double *mats, size_t nmats,
+                      const sv_pauli *paulis, const double *coeffs, size_t nterms,
+                      sv_schedule sched, int reps, sv_options *best, double *best_ms);
+/*
+ * Autotuner of sv_batch_run (same arguments): over the (tile_bits, threads)
+ * pairs the batched kernel is built for (2^tile_bits / threads in {4, 8, 16},
+ * threads 256 or 512), then fuse_max.  Time = device time of the batched
+ * launch (sv_stats.ms[SV_K_BATCH]), minimum over reps after one untimed run.
+ * start (nullable) gives the other options.  Returns the fastest options in
+ * *best and their time in *best_ms (both nullable).  Synchronises.
+ */
+sv_status sv_batch_autotune(int n, sv_dtype dt, int batch,
+                            const sv_gate *gates, const int32_t *gate_off,
+                            const double *params, const int32_t *param_off,
+                            const sv_pauli *paulis, const double *coeffs, size_t nterms,
+                            uint64_t init_index, const sv_options *start, void *stream, int reps,
+                            sv_options *best, double *best_ms);
+
+/* Wait until all work enqueued by the handle has finished. */
+sv_status sv_synchronize(sv_handle *h);
 
 const char *sv_last_error(void);
 const char *sv_version(void);

@@ -68,6 +68,7 @@ PlanOptions plan_options(const sv_options &o) {
     p.evc_low_bits = o.evc_low_bits;
     p.evc_span = o.evc_span;
     p.pad_highest = o.pad_highest != 0;
+    p.fuse_max = o.fuse_max;
     return p;
 }
 
@@ -294,8 +295,15 @@ uint64_t qsu_key(const sv_handle *h, const sv_gate *gates, size_t m, size_t np, 
     return k;
 }
 
+sv_status check_sched(sv_schedule s) {
+    if (s != SV_SCHED_EAGER && s != SV_SCHED_LAZY && s != SV_SCHED_DIRECT && s != SV_SCHED_HIER)
+        return fail(SV_EINVAL, "bad schedule");
+    return SV_OK;
+}
+
 sv_status get_qsu(sv_handle *h, const sv_gate *gates, size_t m, size_t np, sv_schedule sched, QsuEntry **out,
                   sv_stats *st) {
+    SV_TRY(check_sched(sched));
     uint64_t key = qsu_key(h, gates, m, np, sched);
     ++h->tick;
     for (auto &e : h->qsu)
@@ -307,7 +315,10 @@ sv_status get_qsu(sv_handle *h, const sv_gate *gates, size_t m, size_t np, sv_sc
         }
     auto ent = std::make_unique<QsuEntry>();
     auto t0 = std::chrono::steady_clock::now();
-    std::string err = plan_qsu(h->n, h->g, gates, m, sched == SV_SCHED_LAZY, plan_options(h->opt), h->l2p, ent->plan);
+    PlanOptions po = plan_options(h->opt);
+    if (sched == SV_SCHED_HIER) po.hier_intra = h->opt.intra_bits;
+    std::string err = plan_qsu(h->n, sched == SV_SCHED_DIRECT ? 0 : h->g, gates, m, sched != SV_SCHED_EAGER, po,
+                               h->l2p, ent->plan);
     if (!err.empty()) return fail(SV_EINVAL, "QSU plan: " + err);
     ent->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     ent->key = key;
@@ -367,6 +378,8 @@ sv_status evc_entry_upload(sv_handle *h, EvcEntry *ent, const double *coeffs, si
         ss[i].coef = ent->plan.strings[i].coef;
         ss[i].nY = ent->plan.strings[i].nY;
         ss[i].bz = ent->plan.strings[i].bz;
+        ss[i].coef_f = (float)((ent->plan.strings[i].nY & 2) ? -ent->plan.strings[i].coef : ent->plan.strings[i].coef);
+        ss[i].pad = 0;
     }
     SV_CK(upload(ent->groups, gs, h->stream));
     SV_CK(upload(ent->strings, ss, h->stream));
@@ -397,11 +410,11 @@ sv_status check_paulis(const sv_handle *h, const sv_pauli *p, const double *c, s
     return SV_OK;
 }
 
-sv_status get_evc(sv_handle *h, const sv_pauli *p, const double *c, size_t nterms, bool lazy, bool hpsi,
+sv_status get_evc(sv_handle *h, const sv_pauli *p, const double *c, size_t nterms, sv_schedule sched, bool hpsi,
                   EvcEntry **out, sv_stats *st) {
     uint64_t key = hash_bytes(p, nterms * sizeof(sv_pauli));
     key = hash_bytes(c, nterms * sizeof(double), key);
-    int flags = (lazy ? 1 : 0) | (hpsi ? 2 : 0);
+    int flags = (int)sched | (hpsi ? 4 : 0);
     key = hash_bytes(&flags, sizeof(flags), key);
     key = hash_bytes(&h->opt, sizeof(h->opt), key);
     key = hash_bytes(h->l2p.data(), h->l2p.size() * sizeof(int32_t), key);
@@ -417,8 +430,9 @@ sv_status get_evc(sv_handle *h, const sv_pauli *p, const double *c, size_t nterm
     auto ent = std::make_unique<EvcEntry>();
     auto t0 = std::chrono::steady_clock::now();
     PlanOptions po = plan_options(h->opt);
-    std::string err = hpsi ? plan_hpsi(h->n, p, c, nterms, po, h->l2p, ent->plan)
-                           : plan_evc(h->n, h->g, p, c, nterms, lazy, po, h->l2p, ent->plan);
+    std::string err = (hpsi || sched == SV_SCHED_DIRECT)
+                          ? plan_hpsi(h->n, p, c, nterms, po, h->l2p, ent->plan)
+                          : plan_evc(h->n, h->g, p, c, nterms, sched != SV_SCHED_EAGER, po, h->l2p, ent->plan);
     if (!err.empty()) return fail(SV_EINVAL, std::string(hpsi ? "H|psi> plan: " : "EVC plan: ") + err);
     ent->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     ent->key = key;
@@ -778,9 +792,17 @@ sv_status sv_set_options(sv_handle *h, const sv_options *o) {
     if (n.tile_bits > maxstage || n.tile_bits < 5) return fail(SV_EINVAL, "tile_bits must be in [5, 13] (c64) / [5, 12] (c128)");
     if (n.low_bits > n.tile_bits - 4 || n.low_bits < 1) return fail(SV_EINVAL, "low_bits must be in [1, tile_bits - 4]");
     if (n.evc_low_bits + n.evc_span > maxstage) return fail(SV_EINVAL, "evc_low_bits + evc_span too large");
-    if (n.evc_span > kMaxSpan) return fail(SV_EINVAL, "evc_span > 8");
+    if (n.evc_span > kMaxSpan) return fail(SV_EINVAL, "evc_span > 10");
     if (n.threads % 32 || n.threads > 512) return fail(SV_EINVAL, "threads must be a multiple of 32, <= 512");
+    if (n.fuse_max < 0) return fail(SV_EINVAL, "fuse_max must be >= 0");
+    if (n.intra_bits < 0 || n.intra_bits > h->g) return fail(SV_EINVAL, "intra_bits must be in [0, g]");
     h->opt = n;
+    return SV_OK;
+}
+
+sv_status sv_synchronize(sv_handle *h) {
+    SV_TRY(check_handle(h));
+    SV_CK(cudaStreamSynchronize(h->stream));
     return SV_OK;
 }
 
@@ -866,7 +888,8 @@ sv_status sv_expect(sv_handle *h, const sv_pauli *paulis, const double *coeffs, 
         return SV_OK;
     }
     EvcEntry *e = nullptr;
-    SV_TRY(get_evc(h, paulis, coeffs, nterms, sched == SV_SCHED_LAZY, false, &e, st));
+    SV_TRY(check_sched(sched));
+    SV_TRY(get_evc(h, paulis, coeffs, nterms, sched, false, &e, st));
     SV_TRY(status_reset(h));
     SV_TRY(run_evc(h, e, energy, per_term, st));
     if (flags & SV_KEEP_LAYOUT) SV_TRY(relayout(h, entry, false, st));
@@ -885,7 +908,7 @@ sv_status sv_apply_hamiltonian(sv_handle *h, const sv_pauli *paulis, const doubl
     SV_TRY(check_paulis(h, paulis, coeffs, nterms));
     SV_TRY(ensure_psi(h));
     EvcEntry *e = nullptr;
-    SV_TRY(get_evc(h, paulis, coeffs, nterms, true, true, &e, st));
+    SV_TRY(get_evc(h, paulis, coeffs, nterms, SV_SCHED_LAZY, true, &e, st));
     SV_TRY(status_reset(h));
     SV_TRY(run_hpsi(h, e, st));
     if (dst) SV_CK(cudaMemcpyAsync(dst, h->lam, h->state_bytes(), cudaMemcpyDeviceToDevice, h->stream));
@@ -926,7 +949,7 @@ sv_status sv_grad(sv_handle *h, const sv_gate *gates, size_t m, const double *pa
         SV_TRY(run_forward(h, q, st));
     }
     EvcEntry *e = nullptr;
-    SV_TRY(get_evc(h, paulis, coeffs, nterms, true, true, &e, st));
+    SV_TRY(get_evc(h, paulis, coeffs, nterms, SV_SCHED_LAZY, true, &e, st));
     SV_TRY(status_reset(h));
     SV_TRY(run_hpsi(h, e, st));
     SV_TRY(run_reverse(h, q, st));
@@ -996,7 +1019,10 @@ sv_status sv_plan_qsu(int n, int g, const sv_gate *gates, size_t m, sv_schedule 
     for (int q = 0; q < n; ++q) l2p[q] = l2p_init ? l2p_init[q] : q;
     auto *p = new sv_plan();
     p->kind = 0;
-    err = plan_qsu(n, g, gates, m, sched == SV_SCHED_LAZY, plan_options(o), l2p, p->q);
+    SV_TRY(check_sched(sched));
+    PlanOptions po = plan_options(o);
+    if (sched == SV_SCHED_HIER) po.hier_intra = o.intra_bits;
+    err = plan_qsu(n, sched == SV_SCHED_DIRECT ? 0 : g, gates, m, sched != SV_SCHED_EAGER, po, l2p, p->q);
     if (!err.empty()) {
         delete p;
         return fail(SV_EINVAL, err);
@@ -1017,7 +1043,11 @@ sv_status sv_plan_evc(int n, int g, const sv_pauli *paulis, size_t nterms, sv_sc
     std::vector<double> ones(nterms, 1.0);
     auto *p = new sv_plan();
     p->kind = 1;
-    std::string err = plan_evc(n, g, paulis, ones.data(), nterms, sched == SV_SCHED_LAZY, plan_options(o), l2p, p->e);
+    SV_TRY(check_sched(sched));
+    std::string err = sched == SV_SCHED_DIRECT
+                          ? plan_hpsi(n, paulis, ones.data(), nterms, plan_options(o), l2p, p->e)
+                          : plan_evc(n, g, paulis, ones.data(), nterms, sched != SV_SCHED_EAGER, plan_options(o), l2p,
+                                     p->e);
     if (!err.empty()) {
         delete p;
         return fail(SV_EINVAL, err);
@@ -1057,6 +1087,14 @@ sv_status sv_plan_tile(const sv_plan *p, int32_t t, int32_t *begin, int32_t *end
     return SV_OK;
 }
 
+sv_status sv_plan_tile_intra(const sv_plan *p, int32_t t, uint64_t *intra_mask) {
+    if (!p || !intra_mask) return fail(SV_EINVAL, "null argument");
+    const std::vector<Tile> &tiles = p->kind == 0 ? p->q.tiles : p->e.tiles;
+    if (t < 0 || t >= (int32_t)tiles.size()) return fail(SV_EINVAL, "tile index out of range");
+    *intra_mask = tiles[t].intra_mask;
+    return SV_OK;
+}
+
 sv_status sv_plan_pass(const sv_plan *p, int32_t i, int32_t *tile, uint64_t *bits, int32_t *nops, int32_t *ops) {
     if (!p || p->kind != 0) return fail(SV_EINVAL, "not a QSU plan");
     if (i < 0 || i >= (int32_t)p->q.passes.size()) return fail(SV_EINVAL, "pass index out of range");
@@ -1090,10 +1128,20 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     else sv_options_default(dt, &o);
     sv_options d;
     sv_options_default(dt, &d);
-    o.tile_bits = d.tile_bits;           // the batched kernel stages 2^13 (c64) / 2^12 (c128) amplitudes
-    o.evc_low_bits = d.evc_low_bits;
-    o.evc_span = d.evc_span;
+    // the kernel stages 2^tile_bits amplitudes per buffer; H|psi> coset
+    // passes stage at most as many
+    if (o.tile_bits <= 0) o.tile_bits = d.tile_bits;
+    if (o.threads <= 0) o.threads = d.threads;
     if (o.low_bits <= 0) o.low_bits = d.low_bits;
+    if (o.fuse_max < 0) return fail(SV_EINVAL, "fuse_max must be >= 0");
+    if (!batch_supported(dt, o.tile_bits, o.threads))
+        return fail(SV_EINVAL, "sv_batch_run: (tile_bits, threads) must give 2^tile_bits / threads in {4, 8, 16}, "
+                               "tile_bits in [10, 13] (c64) / [10, 12] (c128), threads 256 or 512");
+    if (o.low_bits > o.tile_bits - 4 || o.low_bits < 1) return fail(SV_EINVAL, "low_bits must be in [1, tile_bits - 4]");
+    o.evc_low_bits = d.evc_low_bits;
+    o.evc_span = std::min(d.evc_span, o.tile_bits - o.evc_low_bits);
+    const int kmax = o.tile_bits;
+    const int hio = std::max(8, kmax - o.low_bits);
     const PlanOptions po = plan_options(o);
     std::vector<int32_t> l2p(n);
     for (int q = 0; q < n; ++q) l2p[q] = q;
@@ -1162,6 +1210,8 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
         ss[i].coef = H.strings[i].coef;
         ss[i].nY = H.strings[i].nY;
         ss[i].bz = H.strings[i].bz;
+        ss[i].coef_f = (float)((H.strings[i].nY & 2) ? -H.strings[i].coef : H.strings[i].coef);
+        ss[i].pad = 0;
     }
     std::vector<int32_t> order(batch);
     for (int b = 0; b < batch; ++b) order[b] = b;
@@ -1169,8 +1219,10 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     if (st) st->plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 
     cudaStream_t s0 = (cudaStream_t)stream;
-    const int threads = 512;
-    const int grid = std::min(batch, device_sms());
+    const int threads = o.threads;
+    const int occ = batch_occupancy(dt, kmax, hio, threads);
+    if (occ < 1) return fail(SV_EINVAL, "sv_batch_run: the batched kernel does not fit an SM with these options");
+    const int grid = std::min(batch, device_sms() * occ);
     const size_t es = dt == SV_C64 ? 8 : 16;
     std::vector<DevBuf> bufs(16);
     auto up = [&](int i, const void *src, size_t bytes) -> cudaError_t {
@@ -1215,6 +1267,8 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     a.n = n;
     a.nstates = batch;
     a.nhpass = (int)hp.size();
+    a.kmax = kmax;
+    a.hio = hio;
     a.init_index = init_index;
     a.passes = bufs[0].as<GatePassArgs>();
     a.plan_pass_off = bufs[1].as<int32_t>();

@@ -632,6 +632,25 @@ __device__ __forceinline__ void phase_index(uint32_t rmask, int k, uint32_t &bas
     for (int v = 1; v < (1 << RB); ++v) sp[v] = sp[v & (v - 1)] | rb[__ffs(v) - 1];
 }
 
+// Gate data of a pass staged in shared memory once per CTA: kind, targets and
+// (cos, sin) of the half angle, so that a gate costs one shared load.
+template <typename R>
+struct StagedOp {
+    DevOp op;
+    R c, s;
+};
+
+template <typename R>
+__device__ __forceinline__ void stage_ops(StagedOp<R> *so, const DevOp *ops, int begin, int end, const R *coef) {
+    for (int o = begin + threadIdx.x; o < end; o += blockDim.x) {
+        StagedOp<R> x;
+        x.op = ops[o];
+        x.c = coef[2 * x.op.gate];
+        x.s = coef[2 * x.op.gate + 1];
+        so[o - begin] = x;
+    }
+}
+
 template <typename R, int RB>
 __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, const GatePassArgs a,
                                                      const DevOp *__restrict__ ops, const Phase *__restrict__ phases,
@@ -642,7 +661,9 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
     const uint32_t T = 1u << a.k;
     const uint32_t nh = 1u << (a.k - a.nlow);
     uint64_t *hioff = reinterpret_cast<uint64_t *>(tile + T);
+    StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(hioff + nh);
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
+    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
     __syncthreads();
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
@@ -658,8 +679,11 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
 #pragma unroll
             for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
             for (int o = P.op_begin; o < P.op_end; ++o) {
-                const DevOp op = ops[o];
-                reg_apply<R, RB>(x, op, P.rmask, base, coef, mats, false);
+                const StagedOp<R> x_op = so[o - a.op_begin];
+                DevOp op = x_op.op;
+                const R cs[2] = {x_op.c, x_op.s};
+                op.gate = 0;
+                reg_apply<R, RB>(x, op, P.rmask, base, cs, mats, false);
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) tile[swz_tile(base | sp[v])] = x[v];
@@ -686,8 +710,10 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     Cx<R> *tl = tp + T;
     uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + T);
     double *acc = reinterpret_cast<double *>(hioff + nh);
+    StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(acc + nops * nwarps);
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
     for (int j = threadIdx.x; j < nops * nwarps; j += blockDim.x) acc[j] = 0.0;
+    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
     __syncthreads();
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
@@ -711,8 +737,11 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                 xl[v] = tl[si];
             }
             for (int o = P.op_end - 1; o >= P.op_begin; --o) {
-                const DevOp op = ops[o];
-                R g = reg_adjoint<R, RB>(xp, xl, op, P.rmask, base, coef, mats);
+                const StagedOp<R> x_op = so[o - a.op_begin];
+                DevOp op = x_op.op;
+                const R cs[2] = {x_op.c, x_op.s};
+                op.gate = 0;
+                R g = reg_adjoint<R, RB>(xp, xl, op, P.rmask, base, cs, mats);
                 if (has_param(op.kind)) {
                     g = warp_sum<R>(g);
                     if (lane == 0) acc[(o - a.op_begin) * nwarps + warp] += (double)g;
@@ -947,95 +976,6 @@ __device__ __forceinline__ uint32_t pair_select(const ThreadCoset &tc, uint32_t 
 
 // The same split as (h, s): take the elements j whose bit h equals s, or
 // every element (h = -1, factor 1).
-struct PairSel {
-    int h, s, fac;
-};
-
-__device__ __forceinline__ PairSel pair_split(const ThreadCoset &tc, uint32_t X, int kl, int ept) {
-    const int jb = __ffs(ept) - 1;
-    const uint32_t c = X >> kl;
-    if (c) {
-        const int cb = __ffs(c) - 1;
-        if (cb >= (int)tc.ash) return {cb - (int)tc.ash, 0, 2};
-        const uint32_t cj = c >> tc.ash;
-        for (int h = 0; h < jb; ++h)
-            if (!((cj >> h) & 1u)) return {h, (int)((tc.a0 >> cb) & 1u), 2};
-        return {-1, 0, 1};
-    }
-    if (jb == 0) return {-1, 0, 1};
-    return {0, (int)((tc.l >> (__ffs(X) - 1)) & 1u), 2};
-}
-
-// val with its sign flipped when bit j of sm is set.
-template <int J>
-__device__ __forceinline__ float flip_bit(float v, uint32_t sm) {
-    return __int_as_float(__float_as_int(v) ^ (int)((sm << (31 - J)) & 0x80000000u));
-}
-template <int J>
-__device__ __forceinline__ double flip_bit(double v, uint32_t sm) {
-    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)((sm >> J) & 1u) << 63));
-}
-
-// Sum over the selected elements j = (j' with bit S inserted at H) of the
-// pair term Re or Im(conj(partner) own), signed by sm.  NT = 512, E = EPT*NT.
-template <typename R, int EPT, int H, int S, bool ODD>
-__device__ __forceinline__ R evc_sel_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
-    R a0 = 0, a1 = 0;
-    const uint32_t xl = X & 511u, xh = X >> 9;
-    const Cx<R> *tb = t + (threadIdx.x ^ xl);
-#pragma unroll
-    for (int jp = 0; jp < EPT / 2; ++jp) {
-        constexpr int dummy = 0;
-        (void)dummy;
-        const int j = ((jp >> H) << (H + 1)) | (S << H) | (jp & ((1 << H) - 1));
-        const Cx<R> u = own[j];
-        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
-        const R val = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
-        R f;
-        switch (j) {   // compile-time after unrolling
-#define SV_FB(J) case J: f = flip_bit<J>(val, sm); break;
-            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
-            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
-#undef SV_FB
-        default: f = val; break;
-        }
-        if (jp & 1) a1 += f; else a0 += f;
-    }
-    return a0 + a1;
-}
-
-template <typename R, int EPT, bool ODD>
-__device__ __forceinline__ R evc_all_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
-    R a0 = 0, a1 = 0;
-    const uint32_t xl = X & 511u, xh = X >> 9;
-    const Cx<R> *tb = t + (threadIdx.x ^ xl);
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        const Cx<R> u = own[j];
-        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
-        const R val = X ? (ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y)) : (u.x * u.x + u.y * u.y);
-        const R f = ((sm >> j) & 1u) ? -val : val;
-        if (j & 1) a1 += f; else a0 += f;
-    }
-    return a0 + a1;
-}
-
-// Fast path (NT = 512, E = EPT * 512): dispatch on (h, s, odd).
-template <typename R, int EPT, bool ODD>
-__device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t X, PairSel ps, uint32_t sm) {
-    if (ps.h < 0) return evc_all_loop<R, EPT, ODD>(t, own, X, sm);
-#define SV_SEL(HH)                                                                                       \
-    if (ps.h == HH) {                                                                                    \
-        if constexpr ((1 << (HH + 1)) <= EPT) {                                                          \
-            return ps.s ? evc_sel_loop<R, EPT, HH, 1, ODD>(t, own, X, sm)                                \
-                        : evc_sel_loop<R, EPT, HH, 0, ODD>(t, own, X, sm);                               \
-        }                                                                                                \
-    }
-    SV_SEL(0) SV_SEL(1) SV_SEL(2) SV_SEL(3)
-#undef SV_SEL
-    return (R)0;
-}
-
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                      const DevGroup *__restrict__ groups,
@@ -1154,6 +1094,53 @@ __device__ __forceinline__ R evc_pairs(const Cx<R> *t, const Cx<R> *own, uint32_
     return acc;
 }
 
+// Sign-static EVC term sum over all EPT elements of the thread (NT = 512,
+// E = EPT * 512; every element evaluates its own term, factor 1): the sign
+// of element j is parity(j & W), a compile-time FFMA negation; the partner
+// sits at byte offset B ^ (j << SH) of the staged coset.  DIAG: x = 0, the
+// term is |psi_e|^2.
+template <typename R, int EPT, int W, int KIND>    // KIND 0: even n_Y, 1: odd n_Y, 2: diagonal
+__device__ __forceinline__ R evc_static(const unsigned char *tbytes, const Cx<R> *own, uint32_t B) {
+    constexpr int SH = sizeof(R) == 4 ? 12 : 13;
+    R a0 = 0, a1 = 0;
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const bool neg = (__popc((unsigned)(j & W)) & 1) != 0;
+        const Cx<R> u = own[j];
+        R &a = (j & 1) ? a1 : a0;
+        if (KIND == 2) {
+            if (neg) { a -= u.x * u.x; a -= u.y * u.y; }
+            else { a += u.x * u.x; a += u.y * u.y; }
+        } else {
+            const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
+            if (KIND == 1) {          // Re(i conj(v) u) = v.x u.y - v.y u.x
+                if (neg) { a -= v.x * u.y; a += v.y * u.x; }
+                else { a += v.x * u.y; a -= v.y * u.x; }
+            } else {                  // Re(conj(v) u)
+                if (neg) { a -= v.x * u.x; a -= v.y * u.y; }
+                else { a += v.x * u.x; a += v.y * u.y; }
+            }
+        }
+    }
+    return a0 + a1;
+}
+
+template <typename R, int EPT>
+__device__ __forceinline__ R evc_static_dispatch(const unsigned char *tbytes, const Cx<R> *own, uint32_t B,
+                                                 uint32_t w, int kind) {
+    const uint32_t key = (w & (uint32_t)(EPT - 1)) | ((uint32_t)kind << 4);
+    switch (key) {
+#define SV_ES(W)                                                                   \
+    case W: return evc_static<R, EPT, W, 0>(tbytes, own, B);                       \
+    case W + 16: return evc_static<R, EPT, W, 1>(tbytes, own, B);                  \
+    case W + 32: return evc_static<R, EPT, W, 2>(tbytes, own, B);
+        SV_ES(0) SV_ES(1) SV_ES(2) SV_ES(3) SV_ES(4) SV_ES(5) SV_ES(6) SV_ES(7)
+        SV_ES(8) SV_ES(9) SV_ES(10) SV_ES(11) SV_ES(12) SV_ES(13) SV_ES(14) SV_ES(15)
+#undef SV_ES
+    default: return (R)0;
+    }
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                     const DevGroup *__restrict__ groups,
@@ -1168,7 +1155,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
     R *acc32 = reinterpret_cast<R *>(spanv + (1u << a.m));             // [ng][NT], the state's real type
     uint32_t *pg = reinterpret_cast<uint32_t *>(acc32 + kEvcFew * NT);  // [ng][NT]: sel | tconst << 31
     __shared__ uint64_t gz[kEvcFew];
-    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew];
+    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew], gw[kEvcFew];
     __shared__ int gmeta[kEvcFew];                                      // odd | fac << 1
     __shared__ double wsum[kEvcFew][16];
     coset_span(a, spanv);
@@ -1180,16 +1167,14 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
         const uint32_t sel = G.X ? pair_select(tc, G.X, a.kl, EPT, fac) : 0xFFFFu;
         const int neg0 = G.X ? ((S.nY == 1) | (S.nY == 2)) : 0;
         const int tconst = (__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ neg0) & 1;
-        const PairSel ps = G.X ? pair_split(tc, G.X, a.kl, EPT) : PairSel{-1, 0, 1};
-        // packed: sel (bits 0..15), split bit h + 1 (bits 16..19, 0 = every element),
-        // side s (bit 20), sign constant (bit 31)
-        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | ((uint32_t)(ps.h + 1) << 16) | ((uint32_t)ps.s << 20) |
-                                   ((uint32_t)tconst << 31);
+        // packed: sel (bits 0..15), sign constant (bit 31)
+        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | ((uint32_t)tconst << 31);
         acc32[g * NT + threadIdx.x] = (R)0;
         if (threadIdx.x == 0) {
             gz[g] = S.z;
             gX[g] = G.X;
             gjm[g] = walsh_mask(S.bz >> tc.ash);
+            gw[g] = S.bz >> tc.ash;
             gmeta[g] = (S.nY & 1) | (fac << 1);
         }
     }
@@ -1224,9 +1209,13 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
             const uint32_t sel = X ? (p & 0xFFFFu) : 0xFFFFFFFFu;
             R v;
             if (fast) {
-                const uint32_t sm = base ? ~gjm[g] : gjm[g];
-                const PairSel ps{(int)((p >> 16) & 15u) - 1, (int)((p >> 20) & 1u), 0};
-                v = (meta & 1) ? evc_fast<R, EPT, true>(t, own, X, ps, sm) : evc_fast<R, EPT, false>(t, own, X, ps, sm);
+                // every element evaluates its own term: factor 1
+                v = evc_static_dispatch<R, EPT>(reinterpret_cast<const unsigned char *>(t), own,
+                                                (threadIdx.x ^ X) * (uint32_t)sizeof(Cx<R>), gw[g],
+                                                X == 0u ? 2 : (meta & 1));
+                v = base ? -v : v;
+                acc32[g * NT + threadIdx.x] += v;
+                continue;
             } else if (X == 0u) {
                 v = 0;
 #pragma unroll
@@ -1299,30 +1288,46 @@ __device__ __forceinline__ void hpsi_one(Cx<R> *acc, const Cx<R> *t, uint32_t X,
     }
 }
 
-// Fast path of hpsi_one (NT = 512, E = EPT * 512): compile-time element
-// offsets, the sign as a bit flip of the coefficient.
-template <typename R, int EPT, bool ODD>
-__device__ __forceinline__ void hpsi_fast(Cx<R> *acc, const Cx<R> *t, uint32_t X, uint32_t sm, R g) {
-    const uint32_t xl = X & 511u, xh = X >> 9;
-    const Cx<R> *tb = t + (threadIdx.x ^ xl);
+// Fast path of hpsi_one (NT = 512, E = EPT * 512), sign-static.  The sign of
+// element j is parity(j & W) (W: the string's Walsh index over the j bits,
+// uniform over the CTA) times a per-thread sign already folded into g, so
+// every sign is a compile-time FFMA negation; the partner of element j sits
+// at byte offset B ^ (j << SH) of the staged coset (B = (t ^ X) * amplitude
+// size, SH = log2(512 * amplitude size)), one XOR per element.
+template <int J, int W>
+struct WalshSign {
+    static constexpr bool neg = (__builtin_popcount((unsigned)(J & W)) & 1) != 0;
+};
+
+template <typename R, int EPT, int W, bool ODD>
+__device__ __forceinline__ void hpsi_static(Cx<R> *acc, const unsigned char *tbytes, uint32_t B, R g) {
+    constexpr int SH = sizeof(R) == 4 ? 12 : 13;
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
-        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
-        R f;
-        switch (j) {
-#define SV_FB(J) case J: f = flip_bit<J>(g, sm); break;
-            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
-            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
-#undef SV_FB
-        default: f = g; break;
-        }
+        const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
+        const bool neg = (__popc((unsigned)(j & W)) & 1) != 0;
         if (ODD) {
-            acc[j].x -= f * v.y;
-            acc[j].y += f * v.x;
+            if (neg) { acc[j].x += g * v.y; acc[j].y -= g * v.x; }
+            else { acc[j].x -= g * v.y; acc[j].y += g * v.x; }
         } else {
-            acc[j].x += f * v.x;
-            acc[j].y += f * v.y;
+            if (neg) { acc[j].x -= g * v.x; acc[j].y -= g * v.y; }
+            else { acc[j].x += g * v.x; acc[j].y += g * v.y; }
         }
+    }
+}
+
+template <typename R, int EPT>
+__device__ __forceinline__ void hpsi_static_dispatch(Cx<R> *acc, const unsigned char *tbytes, uint32_t B, R g,
+                                                     uint32_t w, bool odd) {
+    const uint32_t key = (w & (uint32_t)(EPT - 1)) | (odd ? 16u : 0u);
+    switch (key) {
+#define SV_HS(W)                                                               \
+    case W: hpsi_static<R, EPT, W, false>(acc, tbytes, B, g); break;           \
+    case W + 16: hpsi_static<R, EPT, W, true>(acc, tbytes, B, g); break;
+        SV_HS(0) SV_HS(1) SV_HS(2) SV_HS(3) SV_HS(4) SV_HS(5) SV_HS(6) SV_HS(7)
+        SV_HS(8) SV_HS(9) SV_HS(10) SV_HS(11) SV_HS(12) SV_HS(13) SV_HS(14) SV_HS(15)
+#undef SV_HS
+    default: break;
     }
 }
 
@@ -1352,6 +1357,8 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
         const uint64_t ci = blockIdx.x + it * gridDim.x;
         const uint64_t rep = deposit(ci, a.freeb, a.nfree);
         Cx<R> *t = buf + (it & 1) * E;
+        // the coset's previous lambda is loaded into registers while the
+        // strings are applied
         Cx<R> acc[EPT], old[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
@@ -1364,16 +1371,20 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
         __syncthreads();
         for (int gi = a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
+            const uint32_t B = (threadIdx.x ^ G.X) * (uint32_t)sizeof(Cx<R>);
             for (int s = G.s_begin; s < G.s_end; ++s) {
                 const DevString S = strs[s];
                 const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
+                if (fast) {
+                    R g = sizeof(R) == 4 ? (R)S.coef_f : ((S.nY & 2) ? -(R)S.coef : (R)S.coef);
+                    g = base ? -g : g;
+                    hpsi_static_dispatch<R, EPT>(acc, reinterpret_cast<const unsigned char *>(t), B, g,
+                                                 S.bz >> tc.ash, (S.nY & 1) != 0);
+                    continue;
+                }
                 const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                 const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
-                if (fast) {
-                    const uint32_t sm = base ? ~jm : jm;
-                    if (S.nY & 1) hpsi_fast<R, EPT, true>(acc, t, G.X, sm, g);
-                    else hpsi_fast<R, EPT, false>(acc, t, G.X, sm, g);
-                } else if (S.nY & 1) {
+                if (S.nY & 1) {
                     hpsi_one<R, EPT, true>(acc, t, G.X, base, jm, g, E);
                 } else {
                     hpsi_one<R, EPT, false>(acc, t, G.X, base, jm, g, E);
@@ -1435,11 +1446,11 @@ template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int NT = blockDim.x, nwarps = NT >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr uint32_t TILE = sizeof(R) == 4 ? (1u << 13) : (1u << 12);   // staged amplitudes (64 / 64 KiB)
+    const uint32_t TILE = 1u << a.kmax;                              // staged amplitudes per buffer
     Cx<R> *tp = reinterpret_cast<Cx<R> *>(smem);
     Cx<R> *tl = tp + TILE;
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + TILE);       // 2^9 entries (k - nlow <= 9)
-    double *opacc = reinterpret_cast<double *>(hioff + 512);        // [kBatchMaxOps][nwarps]
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + TILE);       // 2^hio entries (>= 2^(k - nlow), >= 256)
+    double *opacc = reinterpret_cast<double *>(hioff + (1u << a.hio));   // [kBatchMaxOps][nwarps]
     R *coef = reinterpret_cast<R *>(opacc + (size_t)kBatchMaxOps * nwarps);   // [2 * kBatchMaxGates]
     __shared__ int s_state;
     __shared__ double s_red[32];
@@ -1753,7 +1764,8 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
 template <typename R>
 cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePassArgs &a, const DevOp *ops,
                               const Phase *phases, const void *coef, const void *mats) {
-    const size_t sm = ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 + 64;
+    const size_t sm = ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
+                      (size_t)(a.op_end - a.op_begin) * sizeof(StagedOp<R>) + 64;
     switch (a.k - 9) {
 #define SV_GR(RB)                                                                                            \
     case RB:                                                                                                 \
@@ -1774,7 +1786,7 @@ cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, co
                              const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
                              int part_stride) {
     const size_t sm = 2 * ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
-                      (size_t)(a.op_end - a.op_begin) * 16 * 8 + 64;
+                      (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) + 64;
     switch (a.k - 9) {
 #define SV_AR(RB)                                                                                            \
     case RB:                                                                                                 \
@@ -2004,25 +2016,57 @@ cudaError_t launch_copy(sv_dtype dt, cudaStream_t st, void *dst, const void *src
     return cudaGetLastError();
 }
 
-size_t batch_smem(sv_dtype dt, int threads) {
+size_t batch_smem(sv_dtype dt, int kmax, int hio, int threads) {
     const size_t es = dt == SV_C64 ? 8 : 16;
-    const size_t tile = dt == SV_C64 ? ((size_t)1 << 13) : ((size_t)1 << 12);
-    return 2 * tile * es + 512 * 8 + (size_t)kBatchMaxOps * (threads / 32) * 8 + 2 * (size_t)kBatchMaxGates * (es / 2);
+    return 2 * ((size_t)1 << kmax) * es + ((size_t)1 << hio) * 8 + (size_t)kBatchMaxOps * (threads / 32) * 8 +
+           2 * (size_t)kBatchMaxGates * (es / 2);
 }
 
 int batch_max_ops() { return kBatchMaxOps; }
 int batch_max_gates() { return kBatchMaxGates; }
 
-cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, const BatchArgs &a) {
-    if (threads != 512) return cudaErrorInvalidValue;
-    const size_t sm = batch_smem(dt, threads);
-    if (dt == SV_C64) {
-        allow_smem(k_batch<float, 16>, sm);
-        k_batch<float, 16><<<grid, threads, sm, st>>>(a);
-    } else {
-        allow_smem(k_batch<double, 8>, sm);
-        k_batch<double, 8><<<grid, threads, sm, st>>>(a);
+// Instantiated kernels: each thread keeps EPT = 2^kmax / threads accumulators
+// of an H|psi> coset pass in registers, EPT in {4, 8, 16}.
+int batch_supported(sv_dtype dt, int kmax, int threads) {
+    if (threads != 256 && threads != 512) return 0;
+    if (kmax < 10 || kmax > (dt == SV_C64 ? 13 : 12)) return 0;
+    const int ept = (1 << kmax) / threads;
+    return ept == 4 || ept == 8 || ept == 16;
+}
+
+#define SV_BATCH_SWITCH(R, ept, ACTION) \
+    switch (ept) {                        \
+    case 4: ACTION(R, 4); break;          \
+    case 8: ACTION(R, 8); break;          \
+    default: ACTION(R, 16); break;        \
     }
+
+int batch_occupancy(sv_dtype dt, int kmax, int hio, int threads) {
+    if (!batch_supported(dt, kmax, threads)) return 0;
+    const size_t sm = batch_smem(dt, kmax, hio, threads);
+    const int ept = (1 << kmax) / threads;
+    int occ = 0;
+#define SV_BOCC(R, E)                       \
+    allow_smem(k_batch<R, E>, sm);          \
+    occ = occupancy(k_batch<R, E>, threads, sm);
+    if (dt == SV_C64) { SV_BATCH_SWITCH(float, ept, SV_BOCC) }
+    else { SV_BATCH_SWITCH(double, ept, SV_BOCC) }
+#undef SV_BOCC
+    return occ;
+}
+
+cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, const BatchArgs &a) {
+    if (!batch_supported(dt, a.kmax, threads)) return cudaErrorInvalidValue;
+    const size_t sm = batch_smem(dt, a.kmax, a.hio, threads);
+    const int ept = (1 << a.kmax) / threads;
+    cudaError_t e = cudaSuccess;
+#define SV_BLAUNCH(R, E)                                      \
+    e = allow_smem(k_batch<R, E>, sm);                        \
+    if (e == cudaSuccess) k_batch<R, E><<<grid, threads, sm, st>>>(a);
+    if (dt == SV_C64) { SV_BATCH_SWITCH(float, ept, SV_BLAUNCH) }
+    else { SV_BATCH_SWITCH(double, ept, SV_BLAUNCH) }
+#undef SV_BLAUNCH
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

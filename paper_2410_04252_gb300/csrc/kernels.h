@@ -39,11 +39,15 @@ struct DevString {
     double coef;
     int32_t nY;
     uint32_t bz;      // parities of the pass's span basis against z
+    float coef_f;     // coef with the sign of i^nY's real factor ((nY & 2) ? -coef : coef), as float
+    int32_t pad;
 };
 
 // Batched kernel arguments (see K-BATCH in kernels.cu).
 struct BatchArgs {
-    int n, nstates, nhpass, init_pad;
+    int n, nstates, nhpass;
+    int kmax;                        // staged amplitudes per buffer: 2^kmax (gate passes and H|psi> cosets)
+    int hio;                         // entries of the high-offset table: 2^hio
     uint64_t init_index;
     const GatePassArgs *passes;      // all plans' gate passes
     const int32_t *plan_pass_off;    // [nplans + 1]
@@ -107,7 +111,10 @@ cudaError_t launch_energy(cudaStream_t st, const double *slotval, const int32_t 
 cudaError_t launch_copy(sv_dtype dt, cudaStream_t st, void *dst, const void *src, size_t n_elems);
 // One persistent launch over all states (512 threads per CTA).
 cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, const BatchArgs &a);
-size_t batch_smem(sv_dtype dt, int threads);
+size_t batch_smem(sv_dtype dt, int kmax, int hio, int threads);
+// 0 when (dt, kmax, threads) has no instantiated kernel
+int batch_supported(sv_dtype dt, int kmax, int threads);
+int batch_occupancy(sv_dtype dt, int kmax, int hio, int threads);
 int batch_max_ops();
 int batch_max_gates();
 

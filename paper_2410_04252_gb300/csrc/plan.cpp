@@ -167,6 +167,60 @@ std::string flat_tiling(int n, int nL, const std::vector<Op> &ops, bool pad_high
     return "";
 }
 
+// Alg. 4 with Alg. 5: flat tiling whose remapping first tries to draw the
+// next local set from Q_L u Q_intra (an intra QR) and only otherwise selects
+// the local and intra sets from all qubits (an inter QR).  Q_intra starts as
+// the logical qubits at physical positions n_L .. n_L + n_intra - 1.
+std::string hierarchical_tiling(int n, int nL, int nintra, const std::vector<Op> &ops, bool pad_highest,
+                                std::vector<int32_t> l2p, std::vector<int32_t> &order, std::vector<Tile> &tiles,
+                                std::vector<int32_t> &final_l2p) {
+    const uint64_t Q = (n == 64) ? ~0ull : (bit(n) - 1);
+    uint64_t cur = local_set(l2p, nL);
+    uint64_t QL = cur, Qintra = 0;
+    for (int q = 0; q < n; ++q)
+        if (l2p[q] >= nL && l2p[q] < nL + nintra) Qintra |= bit(q);
+    std::vector<int32_t> remain = depth_sort(ops), G, next;
+    std::vector<char> taken(ops.size(), 0);
+    int stall = 0;
+    while (!remain.empty()) {
+        tile_construction(QL, remain, ops, G);
+        if (!G.empty()) {
+            Tile t;
+            t.begin = (int32_t)order.size();
+            order.insert(order.end(), G.begin(), G.end());
+            t.end = (int32_t)order.size();
+            t.local_mask = QL;
+            t.intra_mask = Qintra;
+            if (QL != cur) qr_pairs(l2p, cur, QL, t.pairs);
+            t.l2p = l2p;
+            cur = QL;
+            tiles.push_back(std::move(t));
+            for (int32_t u : G) taken[u] = 1;
+            next.clear();
+            for (int32_t u : remain)
+                if (!taken[u]) next.push_back(u);
+            remain.swap(next);
+            stall = 0;
+        } else if (++stall > 1) {
+            return "hierarchical tiling made no progress";
+        }
+        if (remain.empty()) break;
+        const int nl = popc(QL), ni = popc(Qintra);
+        uint64_t QLn = qubit_mapping(QL | Qintra, remain, ops, nl, pad_highest);
+        if (QLn) {
+            Qintra = (QL | Qintra) & ~QLn;
+        } else {
+            QLn = qubit_mapping(Q, remain, ops, nl, pad_highest);
+            const uint64_t Qp = qubit_mapping(Q, remain, ops, nl + ni, pad_highest);
+            Qintra = Qp & ~QLn;
+        }
+        QL = QLn;
+        if (!QL) return "qubit mapping returned an empty set";
+    }
+    final_l2p = l2p;
+    return "";
+}
+
 // The ad hoc rule: depth (or given) order; before an operation with a global
 // target, evict as many locals outside its targets as it has global targets,
 // least recently used first (never used = -1), ties to the highest index.
@@ -224,8 +278,9 @@ std::string adhoc_schedule(int n, int nL, const std::vector<Op> &ops, const std:
 // the earliest remaining gates), padded with the lowest free local bits; the
 // pass then takes gates like Alg. 2 (a gate that does not fit blocks its
 // targets), which keeps the dependency order C1.
-void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low) {
+void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, int fuse_max) {
     const int nL = P.nL;
+    const int cap = (fuse_max > 0 && fuse_max < kMaxPassOps) ? fuse_max : kMaxPassOps;
     k = std::min(k, nL);
     low = std::min(low, k);
     const uint64_t localbits = (nL == 64) ? ~0ull : (bit(nL) - 1);
@@ -251,7 +306,7 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low) {
                 uint64_t t = pm[u];
                 if ((t & ~av) == 0) G.push_back(u);
                 else av &= ~t;
-                if (!av || (int)G.size() >= kMaxPassOps) break;
+                if (!av || (int)G.size() >= cap) break;
             }
             GatePass gp;
             gp.tile = (int32_t)ti;
@@ -715,7 +770,11 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
     }
     P.init_l2p = l2p_init;
     std::string err;
-    if (lazy) {
+    if (lazy && o.hier_intra >= 0) {
+        if (o.hier_intra > g) return "more intra qubits than global qubits";
+        err = hierarchical_tiling(n, P.nL, o.hier_intra, ops, o.pad_highest, l2p_init, P.order, P.tiles,
+                                  P.final_l2p);
+    } else if (lazy) {
         err = flat_tiling(n, P.nL, ops, o.pad_highest, l2p_init, P.order, P.tiles, P.final_l2p);
     } else {
         err = adhoc_schedule(n, P.nL, ops, depth_sort(ops), l2p_init, P.order, P.tiles, P.final_l2p);
@@ -723,7 +782,7 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
     if (!err.empty()) return err;
     if (P.tiles.empty()) P.final_l2p = l2p_init;
     int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
-    plan_gate_passes(P, ops, k, o.low_bits);
+    plan_gate_passes(P, ops, k, o.low_bits, o.fuse_max);
     plan_phases(P);
     return "";
 }

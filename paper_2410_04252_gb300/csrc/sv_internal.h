@@ -10,7 +10,7 @@
 namespace sv {
 
 constexpr int kMaxQubits = 40;
-constexpr int kMaxSpan = 8;          // coset dimension limit of an EVC / H|psi> pass
+constexpr int kMaxSpan = 10;         // coset dimension limit of an EVC / H|psi> pass
 constexpr int kMaxRunBits = 7;       // longest contiguous run of a coset pass (2^7 amplitudes)
 constexpr int kMaxPassStrings = 512; // strings per EVC pass (shared-memory accumulators)
 constexpr int kMaxPassOps = 256;       // gates per shared-memory pass
@@ -32,6 +32,7 @@ struct Tile {
     uint64_t local_mask = 0;         // logical local set Q_L
     std::vector<int32_t> pairs;      // QR before the tile: (local phys, global phys) pairs
     std::vector<int32_t> l2p;        // layout in force during the tile
+    uint64_t intra_mask = 0;         // hierarchical tiling: logical intra set Q_intra (Alg. 4/5)
 };
 
 // Device-side gate of a pass: kind, targets as TILE-LOCAL bit positions.
@@ -119,6 +120,8 @@ struct PlanOptions {
     int tile_bits = 12, low_bits = 5;
     int evc_low_bits = 7, evc_span = 6;
     bool pad_highest = true;
+    int fuse_max = 0;            // gate operations per gate pass (0 = as many as fit)
+    int hier_intra = -1;         // >= 0: hierarchical tiling (Alg. 4/5) with this many intra qubits
 };
 
 // Returns an empty string on success, else the error message.

@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_EPLAN, SV_ETIMEOUT, SV_EDEVICE, SV_ESTATE = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EPLAN", "ETIMEOUT", "EDEVICE", "ESTATE"]
 C64, C128 = 0, 1
-EAGER, LAZY = 0, 1
+EAGER, LAZY, DIRECT, HIER = 0, 1, 2, 3
 KEEP_LAYOUT, FORWARD_DONE = 1, 2
 
 
@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
                 ("evc_low_bits", ctypes.c_int32), ("evc_span", ctypes.c_int32),
                 ("pad_highest", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("wait_limit", ctypes.c_int64), ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("wait_limit", ctypes.c_int64), ("profile", ctypes.c_int32), ("fuse_max", ctypes.c_int32), ("intra_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 K_GATE, K_QR, K_EVC, K_HPSI, K_ADJ, K_PERM, K_AUX, K_BATCH = range(8)
@@ -107,10 +107,17 @@ EXPORTS = {
     "sv_plan_order": (ctypes.c_int, [_vp, _i32p]),
     "sv_plan_tile": (ctypes.c_int, [_vp, _i32, _i32p, _i32p, _u64p, _i32p, _i32p, _i32p]),
     "sv_plan_pass": (ctypes.c_int, [_vp, _i32, _i32p, _u64p, _i32p, _i32p]),
+    "sv_plan_tile_intra": (ctypes.c_int, [_vp, _i32, _u64p]),
     "sv_plan_free": (None, [_vp]),
     "sv_batch_run": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                     _u64, ctypes.POINTER(Options), _vp, _vp, _vp, _vp, ctypes.POINTER(Stats)]),
     "sv_expect_noalloc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _sz, _dp, _vp, _vp]),
+    "sv_autotune": (ctypes.c_int, [_H, _u64, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _vp, _sz, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(Options), _dp]),
+    "sv_batch_autotune": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                         _u64, ctypes.POINTER(Options), _vp, ctypes.c_int, ctypes.POINTER(Options),
+                                         _dp]),
+    "sv_synchronize": (ctypes.c_int, [_H]),
     "sv_last_error": (ctypes.c_char_p, []),
     "sv_version": (ctypes.c_char_p, []),
 }
@@ -119,6 +126,24 @@ for _name, (_res, _args) in EXPORTS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
     _f.argtypes = _args
+
+
+def merge_stats(a: "Stats", b: "Stats") -> "Stats":
+    """Stats of two consecutive calls (a QSU call, then an EVC call) as one:
+    per-kind launches, bytes and times add; plan counters come from the call
+    that owns them."""
+    m = Stats()
+    ctypes.memmove(ctypes.byref(m), ctypes.byref(a), ctypes.sizeof(Stats))
+    for f in ("evc_tiles", "evc_qrs", "evc_passes", "hpsi_passes", "adj_passes"):
+        setattr(m, f, getattr(a, f) + getattr(b, f))
+    m.launches = a.launches + b.launches
+    m.plan_cache_hit = int(a.plan_cache_hit and b.plan_cache_hit)
+    m.plan_ms = a.plan_ms + b.plan_ms
+    for i in range(len(m.kernels)):
+        m.kernels[i] = a.kernels[i] + b.kernels[i]
+        m.bytes[i] = a.bytes[i] + b.bytes[i]
+        m.ms[i] = a.ms[i] + b.ms[i]
+    return m
 
 
 def _check(status):
@@ -320,6 +345,32 @@ class StateVector:
         self.last_stats = st
         return e.value, g, pt
 
+    def synchronize(self):
+        _check(_lib.sv_synchronize(self._h))
+
+    def autotune(self, circ, params, ham=None, schedule: int = LAZY, init_index: int = 0, reps: int = 1,
+                 paulis=None, coeffs=None):
+        """sv_autotune: times the step (vqe_step with a Hamiltonian, else the
+        circuit alone) per candidate option set, leaves the fastest set on the
+        handle and returns (Options, ms)."""
+        if ham is not None:
+            paulis, coeffs = hamiltonian_arrays(ham)
+        nterms = 0
+        if coeffs is not None:
+            coeffs = np.ascontiguousarray(coeffs, np.float64)
+            nterms = len(coeffs)
+            self.ensure_lambda()
+        gates = gate_array(circ)
+        params = np.ascontiguousarray(params, np.float64)
+        mats, nm = _mats(circ)
+        best = Options()
+        ms = ctypes.c_double(0.0)
+        _check(_lib.sv_autotune(self._h, int(init_index), _ptr(gates), circ.m, _ptr(params), params.size,
+                                _ptr(mats) if mats is not None else None, nm,
+                                _ptr(paulis) if nterms else None, _ptr(coeffs) if nterms else None, nterms,
+                                schedule, int(reps), ctypes.byref(best), ctypes.byref(ms)))
+        return best, ms.value
+
 
 # -------------------------------------------------------------- host plans --
 
@@ -336,9 +387,11 @@ def _plan_dict(p, n, is_qsu):
         l2p = np.zeros(n, np.int32)
         _check(_lib.sv_plan_tile(p, t, ctypes.byref(b), ctypes.byref(e), ctypes.byref(lm), ctypes.byref(npairs),
                                  pairs.ctypes.data_as(_i32p), l2p.ctypes.data_as(_i32p)))
+        im = _u64()
+        _check(_lib.sv_plan_tile_intra(p, t, ctypes.byref(im)))
         tiles.append(dict(begin=b.value, end=e.value, local_mask=lm.value,
                           pairs=[(int(pairs[2 * i]), int(pairs[2 * i + 1])) for i in range(npairs.value)],
-                          l2p=[int(v) for v in l2p]))
+                          l2p=[int(v) for v in l2p], intra_mask=im.value))
     passes = []
     if is_qsu:
         for i in range(npass.value):
@@ -393,12 +446,7 @@ def expect_noalloc(state, n: int, dtype: int, paulis, coeffs, stream=None, per_t
     return e.value, pt
 
 
-def batch_run(n: int, dtype: int, circuits, params_list, ham=None, paulis=None, coeffs=None, init_index: int = 0,
-              options: Options | None = None, stream=None):
-    """sv_batch_run over independent states: circuits[b] (workloads.Circuit)
-    with params_list[b].  Returns (energies, list of gradients, times_ns
-    (batch, 2) start/end, Stats)."""
-    import torch
+def _batch_arrays(circuits, params_list, ham, paulis, coeffs):
     if ham is not None:
         paulis, coeffs = hamiltonian_arrays(ham)
     coeffs = np.ascontiguousarray(coeffs, np.float64)
@@ -408,6 +456,16 @@ def batch_run(n: int, dtype: int, circuits, params_list, ham=None, paulis=None, 
     params = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64) for p in params_list]), np.float64)
     param_off = np.zeros(len(circuits) + 1, np.int32)
     param_off[1:] = np.cumsum([len(p) for p in params_list])
+    return gates, gate_off, params, param_off, paulis, coeffs
+
+
+def batch_run(n: int, dtype: int, circuits, params_list, ham=None, paulis=None, coeffs=None, init_index: int = 0,
+              options: Options | None = None, stream=None):
+    """sv_batch_run over independent states: circuits[b] (workloads.Circuit)
+    with params_list[b].  Returns (energies, list of gradients, times_ns
+    (batch, 2) start/end, Stats)."""
+    import torch
+    gates, gate_off, params, param_off, paulis, coeffs = _batch_arrays(circuits, params_list, ham, paulis, coeffs)
     batch = len(circuits)
     energies = np.zeros(batch, np.float64)
     grads = np.zeros(max(params.size, 1), np.float64)
@@ -420,6 +478,22 @@ def batch_run(n: int, dtype: int, circuits, params_list, ham=None, paulis=None, 
                              _ptr(energies), _ptr(grads), _ptr(times), ctypes.byref(st)))
     gl = [grads[param_off[b]:param_off[b + 1]].copy() for b in range(batch)]
     return energies, gl, times.reshape(batch, 2), st
+
+
+def batch_autotune(n: int, dtype: int, circuits, params_list, ham=None, paulis=None, coeffs=None,
+                   init_index: int = 0, options: Options | None = None, stream=None, reps: int = 2):
+    """sv_batch_autotune: returns (fastest Options, device ms of one batched
+    launch with them)."""
+    import torch
+    gates, gate_off, params, param_off, paulis, coeffs = _batch_arrays(circuits, params_list, ham, paulis, coeffs)
+    s = torch.cuda.current_stream() if stream is None else stream
+    best = Options()
+    ms = ctypes.c_double(0.0)
+    _check(_lib.sv_batch_autotune(n, dtype, len(circuits), _ptr(gates), _ptr(gate_off), _ptr(params),
+                                  _ptr(param_off), _ptr(paulis), _ptr(coeffs), len(coeffs), int(init_index),
+                                  ctypes.byref(options) if options is not None else None,
+                                  ctypes.c_void_p(s.cuda_stream), int(reps), ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value
 
 
 def version() -> str:

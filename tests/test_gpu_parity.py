@@ -266,3 +266,54 @@ def test_adjoint_with_forward_checkpoints(every):
     # vqe_step (forward by sv_apply_circuit, gradient with SV_FORWARD_DONE) uses them too
     e2, g2, _ = s1.vqe_step(0, c, params, h, sv.LAZY)
     assert np.max(np.abs(g2 - ps)) < 1e-4 * float(np.abs(h.coeffs).sum())
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+def test_direct_schedule(dtype):
+    """DIRECT (no virtual-chunk constraint, no QR) gives the oracle's state,
+    expectations and gradient."""
+    n, g = 14, 4
+    c = mixed_circuit(n, 80, 123, with_mats=False)
+    p = W.uniform_params(c.nparams, 124, -math.pi, math.pi)
+    s = sv.StateVector(n, g, dtype)
+    s.reset(3)
+    st = s.apply_circuit(c, p, sv.DIRECT)
+    assert st.qsu_qrs == 0
+    ref = oracle_state(c, p, 3)
+    assert np.max(np.abs(s.get_state() - ref)) < AMP_TOL[dtype]
+    ham = W.jw_hamiltonian(n, 200, 125)
+    e, pt = s.expect(ham, sv.DIRECT)
+    assert s.last_stats.evc_qrs == 0
+    tol = 1e-4 * l1(ham) if dtype == sv.C64 else 1e-10 * l1(ham)
+    assert abs(e - oracle.energy(ref, ham)) < tol
+    h2 = W.random_hamiltonian(n, 64, 126)
+    e2, gr, _ = s.vqe_step(0, c, p, h2, sv.DIRECT)
+    tol2 = 1e-4 * l1(h2) if dtype == sv.C64 else 1e-7
+    assert abs(e2 - ograd.objective(c, p, h2)) < tol2
+    # Givens / double-excitation parameters: central differences
+    assert np.max(np.abs(gr - ograd.finite_difference(c, p, h2))) < tol2
+
+
+@pytest.mark.parametrize("ni", [0, 1, 3])
+def test_hierarchical_schedule(ni):
+    """QSU under hierarchical tiling (Alg. 4/5) gives the oracle's state; its
+    layout is the oracle planner's; the gradient under it is the oracle's."""
+    n, g = 13, 3
+    c = W.fabric_circuit(n, 6)
+    p = W.uniform_params(c.nparams, 131, -math.pi, math.pi)
+    init = W.half_filled_index(n)
+    o = sv.default_options(sv.C64)
+    o.intra_bits = ni
+    s = sv.StateVector(n, g, sv.C64, options=o)
+    s.reset(init)
+    s.apply_circuit(c, p, sv.HIER)
+    T = [c.targets(i) for i in range(c.m)]
+    plan = P.hierarchical_tiling(n, T, n - g, ni)
+    assert list(s.permutation()) == plan.perms[-1]
+    ref = oracle_state(c, p, init)
+    assert np.max(np.abs(s.get_state() - ref)) < AMP_TOL[sv.C64]
+    h = W.jw_hamiltonian(n, 90, 132)
+    s.reset(init)
+    e, gr = s.grad(c, p, h, sv.HIER)
+    assert abs(e - ograd.objective(c, p, h, init)) < 1e-4 * l1(h)
+    assert np.max(np.abs(gr - ograd.finite_difference(c, p, h, init))) < 1e-4 * l1(h)

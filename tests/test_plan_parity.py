@@ -136,3 +136,118 @@ def test_invalid_inputs_rejected():
     p = sv.plan_evc(6, 2, [0b111111, 0b11], [0, 0], sv.LAZY)
     assert p["order"][-1] == 0 and not p["tiles"][-1]["pairs"]
     del c
+
+
+@pytest.mark.parametrize("fuse_max", [1, 3, 8])
+def test_fusion_depth_caps_pass_size(fuse_max):
+    """fuse_max bounds the gate operations of every pass; every operation is
+    still scheduled exactly once and in a C1-respecting order."""
+    n, g = 14, 3
+    c = W.hea_circuit(n, 3)
+    o = sv.default_options(sv.C64)
+    o.fuse_max = fuse_max
+    plan = sv.plan_qsu(n, g, c, sv.LAZY, o)
+    free = sv.plan_qsu(n, g, c, sv.LAZY)
+    assert max(len(ps["ops"]) for ps in plan["passes"]) <= fuse_max
+    assert len(plan["passes"]) > len(free["passes"])
+    ops = [u for ps in plan["passes"] for u in ps["ops"]]
+    assert sorted(ops) == list(range(c.m))
+    # C1: gates sharing a qubit keep their input order
+    pos = {u: i for i, u in enumerate(ops)}
+    for a in range(c.m):
+        for b in range(a + 1, c.m):
+            if set(c.targets(a)) & set(c.targets(b)):
+                assert pos[a] < pos[b]
+
+
+def test_direct_schedule_has_one_tile_and_no_qr():
+    """DIRECT drops the virtual-chunk constraint: one tile, no QR, every
+    gate and string scheduled exactly once."""
+    n, g = 16, 4
+    c = W.hea_circuit(n, 3)
+    plan = sv.plan_qsu(n, g, c, sv.DIRECT)
+    assert len(plan["tiles"]) == 1
+    assert all(len(t["pairs"]) == 0 for t in plan["tiles"])
+    assert sorted(u for ps in plan["passes"] for u in ps["ops"]) == list(range(c.m))
+    ham = W.random_hamiltonian(n, 64, 5)
+    x, z = W.pauli_masks(ham)
+    ep = sv.plan_evc(n, g, x, z, sv.DIRECT)
+    assert len(ep["tiles"]) == 1 and len(ep["tiles"][0]["pairs"]) == 0
+    assert sorted(ep["order"]) == list(range(len(ham.coeffs)))
+    with pytest.raises(sv.SvError):
+        sv.plan_qsu(n, g, c, 7)
+
+
+def _golden(name):
+    import os
+    d = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if "=" in line:
+                k, v = line.split("=", 1)
+                d[k.strip()] = v.strip()
+    return d
+
+
+def _hier_opt(ni):
+    o = sv.default_options()
+    o.intra_bits = ni
+    return o
+
+
+def _same_hier(lib, orc, n):
+    _same_qsu(lib, orc)
+    assert [t["intra_mask"] for t in lib["tiles"]] == [sum(1 << q for q in I) for I in orc.intra]
+
+
+def test_hierarchical_plan_matches_oracle():
+    """Alg. 4/5 in the library planner == the oracle's, on random circuits and
+    every intra size."""
+    for seed in range(30):
+        n = 8 + seed % 7
+        g = 2 + seed % 3
+        c = W.random_circuit(n, 40 + 3 * (seed % 5), 700 + seed)
+        T = [c.targets(i) for i in range(c.m)]
+        for ni in range(0, g + 1):
+            lib = sv.plan_qsu(n, g, c, sv.HIER, _hier_opt(ni))
+            _same_hier(lib, P.hierarchical_tiling(n, T, n - g, ni), n)
+
+
+def test_fig9_from_library_planner():
+    gd = _golden("fig9_hierarchical_tiling.txt")
+    n, nL, ni = int(gd["n"]), int(gd["n_local"]), int(gd["n_intra"])
+    c = W.fabric_blocks_circuit(n, int(gd["layers"]))
+    lib = sv.plan_qsu(n, n - nL, c, sv.HIER, _hier_opt(ni))
+    assert [t["begin"] for t in lib["tiles"]] == [int(v) for v in gd["first_gate_of_tile"].split()]
+    intra = [{q for q in range(n) if t["intra_mask"] >> q & 1} for t in lib["tiles"]]
+    want = [set(int(x) for x in s.split(",")) for s in gd["intra_sets"].split("|")]
+    assert intra == want
+    inter = [set(range(n)) - {q for q in range(n) if (t["local_mask"] | t["intra_mask"]) >> q & 1}
+             for t in lib["tiles"]]
+    kinds = ["inter" if inter[i] != inter[i - 1] else "intra" for i in range(1, len(inter))]
+    assert kinds == gd["qr_kinds"].split()
+
+
+def test_hierarchical_rejects_too_many_intra_qubits():
+    c = W.hea_circuit(10, 2)
+    with pytest.raises(sv.SvError):
+        sv.plan_qsu(10, 2, c, sv.HIER, _hier_opt(3))
+
+
+def test_qsu_experiment_qr_trends():
+    """Plan-level QSU experiment (Sec. V-B-1, GateFabric, 4n layers, g = 5):
+    flat tiling's QR count does not grow with n, the ad hoc count grows with
+    the layers, and at n = 30 the ratio lies in a band around the paper's 71
+    (the ad hoc rule is not fully specified, so the ratio is a sanity band,
+    not a pin)."""
+    g = 5
+    flat, adhoc = [], []
+    for n in (20, 24, 28, 30, 32):
+        c = W.fabric_blocks_circuit(n, 4 * n)
+        flat.append(sum(1 for t in sv.plan_qsu(n, g, c, sv.LAZY)["tiles"] if t["pairs"]))
+        adhoc.append(sum(1 for t in sv.plan_qsu(n, g, c, sv.EAGER)["tiles"] if t["pairs"]))
+    assert all(b <= a for a, b in zip(flat, flat[1:]))
+    assert all(b > a for a, b in zip(adhoc, adhoc[1:]))
+    ratio = adhoc[3] / flat[3]
+    assert 71 / 2 < ratio < 71 * 2
