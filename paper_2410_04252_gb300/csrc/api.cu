@@ -378,8 +378,6 @@ sv_status evc_entry_upload(sv_handle *h, EvcEntry *ent, const double *coeffs, si
         ss[i].coef = ent->plan.strings[i].coef;
         ss[i].nY = ent->plan.strings[i].nY;
         ss[i].bz = ent->plan.strings[i].bz;
-        ss[i].coef_f = (float)((ent->plan.strings[i].nY & 2) ? -ent->plan.strings[i].coef : ent->plan.strings[i].coef);
-        ss[i].pad = 0;
     }
     SV_CK(upload(ent->groups, gs, h->stream));
     SV_CK(upload(ent->strings, ss, h->stream));
@@ -1210,8 +1208,6 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
         ss[i].coef = H.strings[i].coef;
         ss[i].nY = H.strings[i].nY;
         ss[i].bz = H.strings[i].bz;
-        ss[i].coef_f = (float)((H.strings[i].nY & 2) ? -H.strings[i].coef : H.strings[i].coef);
-        ss[i].pad = 0;
     }
     std::vector<int32_t> order(batch);
     for (int b = 0; b < batch; ++b) order[b] = b;

@@ -409,6 +409,16 @@ __global__ void __launch_bounds__(512) k_adj_pass(Cx<R> *__restrict__ psi, Cx<R>
     }
 }
 
+// ---------------------------------------------------------- cp.async --
+// 16-byte asynchronous global -> shared copies with commit / wait groups.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // ------------------------------------------------- register-blocked passes --
 // A pass of RY / RZ / CZ / 1-qubit matrices runs in phases (host planned):
 // in a phase each of the 512 threads holds the 2^RB amplitudes spanned by
@@ -651,25 +661,51 @@ __device__ __forceinline__ void stage_ops(StagedOp<R> *so, const DevOp *ops, int
     }
 }
 
+// One amplitude (8 or 16 bytes) copied global -> shared asynchronously.
+template <typename R>
+__device__ __forceinline__ void cp_async_amp(Cx<R> *dst, const Cx<R> *src) {
+    if (sizeof(Cx<R>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// Issue the copies of one gate-pass tile (swizzled layout) into shared memory.
+template <typename R>
+__device__ __forceinline__ void load_tile_async(Cx<R> *tile, const Cx<R> *psi, uint64_t gbase,
+                                                const uint64_t *hioff, int nlow, uint32_t T) {
+    const uint32_t lowmask = (1u << nlow) - 1u;
+    for (uint32_t j = threadIdx.x; j < T; j += blockDim.x)
+        cp_async_amp<R>(&tile[swz_tile(j)], &psi[gbase | hioff[j >> nlow] | (j & lowmask)]);
+}
+
 template <typename R, int RB>
 __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, const GatePassArgs a,
                                                      const DevOp *__restrict__ ops, const Phase *__restrict__ phases,
                                                      const R *__restrict__ coef, const Cx<R> *__restrict__ mats) {
     constexpr int V = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem[];
-    Cx<R> *tile = reinterpret_cast<Cx<R> *>(smem);
     const uint32_t T = 1u << a.k;
     const uint32_t nh = 1u << (a.k - a.nlow);
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(tile + T);
+    Cx<R> *tiles = reinterpret_cast<Cx<R> *>(smem);          // two tiles: the next one streams in
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(tiles + 2 * T);
     StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(hioff + nh);
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
     stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
     __syncthreads();
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
-    for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    for (uint64_t k = 0; k < 2; ++k) {
+        if (k < mine)
+            load_tile_async<R>(tiles + k * T, psi, deposit(blockIdx.x + k * gridDim.x, a.out, a.nout), hioff, a.nlow, T);
+        cp_async_commit();
+    }
+    for (uint64_t it = 0; it < mine; ++it) {
+        const uint64_t ti = blockIdx.x + it * gridDim.x;
         const uint64_t gbase = deposit(ti, a.out, a.nout);
-        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) tile[swz_tile(j)] = psi[gbase | hioff[j >> a.nlow] | (j & lowmask)];
+        Cx<R> *tile = tiles + (it & 1) * T;
+        cp_async_wait1();
         __syncthreads();
         for (int ph = a.ph_begin; ph < a.ph_end; ++ph) {
             const Phase P = phases[ph];
@@ -691,10 +727,13 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
         }
         for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = tile[swz_tile(j)];
         __syncthreads();
+        if (it + 2 < mine)
+            load_tile_async<R>(tile, psi, deposit(ti + 2 * gridDim.x, a.out, a.nout), hioff, a.nlow, T);
+        cp_async_commit();
     }
 }
 
-template <typename R, int RB>
+template <typename R, int RB, bool PREF>
 __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
                                                     const GatePassArgs a, const DevOp *__restrict__ ops,
                                                     const Phase *__restrict__ phases, const R *__restrict__ coef,
@@ -706,9 +745,11 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const uint32_t nh = 1u << (a.k - a.nlow);
     const int nops = a.op_end - a.op_begin;
     const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    Cx<R> *tp = reinterpret_cast<Cx<R> *>(smem);
-    Cx<R> *tl = tp + T;
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + T);
+    // shared memory: lambda tile, then psi tiles (two when PREF: the next
+    // tile's psi streams in while the current one is processed)
+    Cx<R> *tl = reinterpret_cast<Cx<R> *>(smem);
+    Cx<R> *tps = tl + T;
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(tps + (PREF ? 2 : 1) * T);
     double *acc = reinterpret_cast<double *>(hioff + nh);
     StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(acc + nops * nwarps);
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
@@ -717,13 +758,27 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     __syncthreads();
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
-    for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (PREF) {
+        if (mine > 0) load_tile_async<R>(tps, psi, deposit(blockIdx.x, a.out, a.nout), hioff, a.nlow, T);
+        cp_async_commit();
+    }
+    for (uint64_t it = 0; it < mine; ++it) {
+        const uint64_t ti = blockIdx.x + it * gridDim.x;
         const uint64_t gbase = deposit(ti, a.out, a.nout);
+        Cx<R> *tp = tps + (PREF ? (it & 1) * T : 0);
+        if (PREF) {
+            if (it + 1 < mine)
+                load_tile_async<R>(tps + ((it + 1) & 1) * T, psi, deposit(ti + gridDim.x, a.out, a.nout), hioff,
+                                   a.nlow, T);
+            cp_async_commit();
+        }
         for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
             const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
-            tp[swz_tile(j)] = psi[gi];
+            if (!PREF) tp[swz_tile(j)] = psi[gi];
             tl[swz_tile(j)] = lam[gi];
         }
+        if (PREF) cp_async_wait1();
         __syncthreads();
         for (int ph = a.ph_end - 1; ph >= a.ph_begin; --ph) {
             const Phase P = phases[ph];
@@ -813,7 +868,12 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
     Cx<R> *A = reinterpret_cast<Cx<R> *>(smem);
     Cx<R> *B = A + T;
     uint64_t *hioff = reinterpret_cast<uint64_t *>(B + T);
+    // source slot (swizzled, after the in-tile exchanges) of every tile index,
+    // two 16-bit entries per 32-bit word: computed once per CTA
+    uint32_t *pt = reinterpret_cast<uint32_t *>(hioff + nh);
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.tb, a.ntb - a.L);
+    for (uint32_t q = threadIdx.x; q < T / 2; q += blockDim.x)
+        pt[q] = swz<R>(sigma_lo(2 * q, a)) | (swz<R>(sigma_lo(2 * q + 1, a)) << 16);
     __syncthreads();
     const uint32_t runmask = (1u << a.L) - 1u;
     const uint64_t ntiles = 1ull << a.nout;
@@ -843,7 +903,7 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
         if (vec) {
             for (uint32_t j = 2 * threadIdx.x; j < T; j += 2 * blockDim.x) {
                 const uint64_t off = hioff[j >> a.L] | (j & runmask);
-                const uint32_t s0 = swz<R>(sigma_lo(j, a)), s1 = swz<R>(sigma_lo(j + 1, a));
+                const uint32_t pp = pt[j >> 1], s0 = pp & 0xFFFFu, s1 = pp >> 16;
                 const Cx<R> *src = self ? A : B;
                 float4 v;
                 v.x = src[s0].x; v.y = src[s0].y; v.z = src[s1].x; v.w = src[s1].y;
@@ -857,7 +917,7 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
         } else {
             for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
                 const uint64_t off = hioff[j >> a.L] | (j & runmask);
-                const uint32_t s = swz<R>(sigma_lo(j, a));
+                const uint32_t s = (j & 1) ? (pt[j >> 1] >> 16) : (pt[j >> 1] & 0xFFFFu);
                 psi[b0 | off] = self ? A[s] : B[s];
                 if (!self) psi[b1 | off] = A[s];
             }
@@ -872,13 +932,6 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
 // coset's copies are in flight while the current one is processed
 // (commit/wait groups: at iteration i, groups i and i+1 are outstanding and
 // waiting for all but the newest completes coset i).
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <typename R>
 __device__ __forceinline__ void load_coset(Cx<R> *dst, const Cx<R> *psi, uint64_t rep, const uint64_t *spanv, int kl,
@@ -976,6 +1029,96 @@ __device__ __forceinline__ uint32_t pair_select(const ThreadCoset &tc, uint32_t 
 
 // The same split as (h, s): take the elements j whose bit h equals s, or
 // every element (h = -1, factor 1).
+struct PairSel {
+    int h, s, fac;
+};
+
+__device__ __forceinline__ PairSel pair_split(const ThreadCoset &tc, uint32_t X, int kl, int ept) {
+    const int jb = __ffs(ept) - 1;
+    const uint32_t c = X >> kl;
+    if (c) {
+        const int cb = __ffs(c) - 1;
+        if (cb >= (int)tc.ash) return {cb - (int)tc.ash, 0, 2};
+        const uint32_t cj = c >> tc.ash;
+        for (int h = 0; h < jb; ++h)
+            if (!((cj >> h) & 1u)) return {h, (int)((tc.a0 >> cb) & 1u), 2};
+        return {-1, 0, 1};
+    }
+    if (jb == 0) return {-1, 0, 1};
+    return {0, (int)((tc.l >> (__ffs(X) - 1)) & 1u), 2};
+}
+
+// val with its sign flipped when bit j of sm is set.
+template <int J>
+__device__ __forceinline__ float flip_bit(float v, uint32_t sm) {
+    return __int_as_float(__float_as_int(v) ^ (int)((sm << (31 - J)) & 0x80000000u));
+}
+template <int J>
+__device__ __forceinline__ double flip_bit(double v, uint32_t sm) {
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)((sm >> J) & 1u) << 63));
+}
+
+// Sum over the selected elements j = (j' with bit S inserted at H) of the
+// pair term Re or Im(conj(partner) own), signed by sm.  NT = 2^LOGNT, E = EPT*NT.
+template <typename R, int EPT, int H, int S, bool ODD, int LOGNT>
+__device__ __forceinline__ R evc_sel_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
+    constexpr int SH = LOGNT + (sizeof(R) == 4 ? 3 : 4);
+    R a0 = 0, a1 = 0;
+    // partner of element j: byte offset B ^ (j << SH) of the staged coset
+    const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(t);
+    const uint32_t B = (threadIdx.x ^ X) * (uint32_t)sizeof(Cx<R>);
+#pragma unroll
+    for (int jp = 0; jp < EPT / 2; ++jp) {
+        const int j = ((jp >> H) << (H + 1)) | (S << H) | (jp & ((1 << H) - 1));
+        const Cx<R> u = own[j];
+        const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
+        const R val = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
+        R f;
+        switch (j) {   // compile-time after unrolling
+#define SV_FB(J) case J: f = flip_bit<J>(val, sm); break;
+            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
+            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
+#undef SV_FB
+        default: f = val; break;
+        }
+        if (jp & 1) a1 += f; else a0 += f;
+    }
+    return a0 + a1;
+}
+
+template <typename R, int EPT, bool ODD, int LOGNT>
+__device__ __forceinline__ R evc_all_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
+    constexpr int SH = LOGNT + (sizeof(R) == 4 ? 3 : 4);
+    R a0 = 0, a1 = 0;
+    const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(t);
+    const uint32_t B = (threadIdx.x ^ X) * (uint32_t)sizeof(Cx<R>);
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const Cx<R> u = own[j];
+        const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
+        const R val = X ? (ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y)) : (u.x * u.x + u.y * u.y);
+        const R f = ((sm >> j) & 1u) ? -val : val;
+        if (j & 1) a1 += f; else a0 += f;
+    }
+    return a0 + a1;
+}
+
+// Fast path (NT = 2^LOGNT, E = EPT * NT): dispatch on (h, s, odd).
+template <typename R, int EPT, bool ODD, int LOGNT>
+__device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t X, PairSel ps, uint32_t sm) {
+    if (ps.h < 0) return evc_all_loop<R, EPT, ODD, LOGNT>(t, own, X, sm);
+#define SV_SEL(HH)                                                                                       \
+    if (ps.h == HH) {                                                                                    \
+        if constexpr ((1 << (HH + 1)) <= EPT) {                                                          \
+            return ps.s ? evc_sel_loop<R, EPT, HH, 1, ODD, LOGNT>(t, own, X, sm)                                \
+                        : evc_sel_loop<R, EPT, HH, 0, ODD, LOGNT>(t, own, X, sm);                               \
+        }                                                                                                \
+    }
+    SV_SEL(0) SV_SEL(1) SV_SEL(2) SV_SEL(3)
+#undef SV_SEL
+    return (R)0;
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                      const DevGroup *__restrict__ groups,
@@ -1094,55 +1237,8 @@ __device__ __forceinline__ R evc_pairs(const Cx<R> *t, const Cx<R> *own, uint32_
     return acc;
 }
 
-// Sign-static EVC term sum over all EPT elements of the thread (NT = 512,
-// E = EPT * 512; every element evaluates its own term, factor 1): the sign
-// of element j is parity(j & W), a compile-time FFMA negation; the partner
-// sits at byte offset B ^ (j << SH) of the staged coset.  DIAG: x = 0, the
-// term is |psi_e|^2.
-template <typename R, int EPT, int W, int KIND>    // KIND 0: even n_Y, 1: odd n_Y, 2: diagonal
-__device__ __forceinline__ R evc_static(const unsigned char *tbytes, const Cx<R> *own, uint32_t B) {
-    constexpr int SH = sizeof(R) == 4 ? 12 : 13;
-    R a0 = 0, a1 = 0;
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        const bool neg = (__popc((unsigned)(j & W)) & 1) != 0;
-        const Cx<R> u = own[j];
-        R &a = (j & 1) ? a1 : a0;
-        if (KIND == 2) {
-            if (neg) { a -= u.x * u.x; a -= u.y * u.y; }
-            else { a += u.x * u.x; a += u.y * u.y; }
-        } else {
-            const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
-            if (KIND == 1) {          // Re(i conj(v) u) = v.x u.y - v.y u.x
-                if (neg) { a -= v.x * u.y; a += v.y * u.x; }
-                else { a += v.x * u.y; a -= v.y * u.x; }
-            } else {                  // Re(conj(v) u)
-                if (neg) { a -= v.x * u.x; a -= v.y * u.y; }
-                else { a += v.x * u.x; a += v.y * u.y; }
-            }
-        }
-    }
-    return a0 + a1;
-}
-
-template <typename R, int EPT>
-__device__ __forceinline__ R evc_static_dispatch(const unsigned char *tbytes, const Cx<R> *own, uint32_t B,
-                                                 uint32_t w, int kind) {
-    const uint32_t key = (w & (uint32_t)(EPT - 1)) | ((uint32_t)kind << 4);
-    switch (key) {
-#define SV_ES(W)                                                                   \
-    case W: return evc_static<R, EPT, W, 0>(tbytes, own, B);                       \
-    case W + 16: return evc_static<R, EPT, W, 1>(tbytes, own, B);                  \
-    case W + 32: return evc_static<R, EPT, W, 2>(tbytes, own, B);
-        SV_ES(0) SV_ES(1) SV_ES(2) SV_ES(3) SV_ES(4) SV_ES(5) SV_ES(6) SV_ES(7)
-        SV_ES(8) SV_ES(9) SV_ES(10) SV_ES(11) SV_ES(12) SV_ES(13) SV_ES(14) SV_ES(15)
-#undef SV_ES
-    default: return (R)0;
-    }
-}
-
-template <typename R, int EPT>
-__global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ psi, const CosetArgs a,
+template <typename R, int EPT, int LOGNT>
+__global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                     const DevGroup *__restrict__ groups,
                                                     const DevString *__restrict__ strs, double *__restrict__ part,
                                                     int part_stride) {
@@ -1155,9 +1251,11 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
     R *acc32 = reinterpret_cast<R *>(spanv + (1u << a.m));             // [ng][NT], the state's real type
     uint32_t *pg = reinterpret_cast<uint32_t *>(acc32 + kEvcFew * NT);  // [ng][NT]: sel | tconst << 31
     __shared__ uint64_t gz[kEvcFew];
-    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew], gw[kEvcFew];
+    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew];
     __shared__ int gmeta[kEvcFew];                                      // odd | fac << 1
-    __shared__ double wsum[kEvcFew][16];
+    __shared__ double wsum[kEvcFew][32];                                // FP64 per string and warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < kEvcFew * 32; j += NT) wsum[j / 32][j % 32] = 0.0;
     coset_span(a, spanv);
     const ThreadCoset tc = thread_coset(a.kl);
     for (int g = 0; g < ng; ++g) {
@@ -1167,24 +1265,23 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
         const uint32_t sel = G.X ? pair_select(tc, G.X, a.kl, EPT, fac) : 0xFFFFu;
         const int neg0 = G.X ? ((S.nY == 1) | (S.nY == 2)) : 0;
         const int tconst = (__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ neg0) & 1;
-        // packed: sel (bits 0..15), sign constant (bit 31)
-        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | ((uint32_t)tconst << 31);
+        const PairSel ps = G.X ? pair_split(tc, G.X, a.kl, EPT) : PairSel{-1, 0, 1};
+        // packed: sel (bits 0..15), split bit h + 1 (bits 16..19, 0 = every element),
+        // side s (bit 20), sign constant (bit 31)
+        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | ((uint32_t)(ps.h + 1) << 16) | ((uint32_t)ps.s << 20) |
+                                   ((uint32_t)tconst << 31);
         acc32[g * NT + threadIdx.x] = (R)0;
         if (threadIdx.x == 0) {
             gz[g] = S.z;
             gX[g] = G.X;
             gjm[g] = walsh_mask(S.bz >> tc.ash);
-            gw[g] = S.bz >> tc.ash;
             gmeta[g] = (S.nY & 1) | (fac << 1);
         }
     }
     __syncthreads();
-    double d[kEvcFew];
-#pragma unroll
-    for (int g = 0; g < kEvcFew; ++g) d[g] = 0.0;
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    const bool fast = (NT == 512) && (E == (uint32_t)EPT * 512u) && EPT >= 2;
+    const bool fast = (NT == (1 << LOGNT)) && (E == ((uint32_t)EPT << LOGNT)) && EPT >= 2;
     for (uint64_t k = 0; k < 2; ++k) {
         if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
         cp_async_commit();
@@ -1209,13 +1306,10 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
             const uint32_t sel = X ? (p & 0xFFFFu) : 0xFFFFFFFFu;
             R v;
             if (fast) {
-                // every element evaluates its own term: factor 1
-                v = evc_static_dispatch<R, EPT>(reinterpret_cast<const unsigned char *>(t), own,
-                                                (threadIdx.x ^ X) * (uint32_t)sizeof(Cx<R>), gw[g],
-                                                X == 0u ? 2 : (meta & 1));
-                v = base ? -v : v;
-                acc32[g * NT + threadIdx.x] += v;
-                continue;
+                const uint32_t sm = base ? ~gjm[g] : gjm[g];
+                const PairSel ps{(int)((p >> 16) & 15u) - 1, (int)((p >> 20) & 1u), 0};
+                v = (meta & 1) ? evc_fast<R, EPT, true, LOGNT>(t, own, X, ps, sm)
+                               : evc_fast<R, EPT, false, LOGNT>(t, own, X, ps, sm);
             } else if (X == 0u) {
                 v = 0;
 #pragma unroll
@@ -1233,26 +1327,17 @@ __global__ void __launch_bounds__(512, 1) k_evc_few(const Cx<R> *__restrict__ ps
             acc32[g * NT + threadIdx.x] += v * (R)(meta >> 1);
         }
         if ((it & 63) == 63 || it + 1 == mine) {
-#pragma unroll
-            for (int g = 0; g < kEvcFew; ++g) {
-                if (g < ng) {
-                    d[g] += (double)acc32[g * NT + threadIdx.x];
-                    acc32[g * NT + threadIdx.x] = (R)0;
-                }
+            // flush: FP64 warp sums into the per-warp slots (fixed order)
+            for (int g = 0; g < ng; ++g) {
+                double v = (double)acc32[g * NT + threadIdx.x];
+                acc32[g * NT + threadIdx.x] = (R)0;
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) wsum[g][warp] += v;
             }
         }
         __syncthreads();
         if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
         cp_async_commit();
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int g = 0; g < kEvcFew; ++g) {
-        if (g < ng) {
-            double v = d[g];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wsum[g][warp] = v;
-        }
     }
     __syncthreads();
     if (threadIdx.x < ng) {
@@ -1288,46 +1373,30 @@ __device__ __forceinline__ void hpsi_one(Cx<R> *acc, const Cx<R> *t, uint32_t X,
     }
 }
 
-// Fast path of hpsi_one (NT = 512, E = EPT * 512), sign-static.  The sign of
-// element j is parity(j & W) (W: the string's Walsh index over the j bits,
-// uniform over the CTA) times a per-thread sign already folded into g, so
-// every sign is a compile-time FFMA negation; the partner of element j sits
-// at byte offset B ^ (j << SH) of the staged coset (B = (t ^ X) * amplitude
-// size, SH = log2(512 * amplitude size)), one XOR per element.
-template <int J, int W>
-struct WalshSign {
-    static constexpr bool neg = (__builtin_popcount((unsigned)(J & W)) & 1) != 0;
-};
-
-template <typename R, int EPT, int W, bool ODD>
-__device__ __forceinline__ void hpsi_static(Cx<R> *acc, const unsigned char *tbytes, uint32_t B, R g) {
-    constexpr int SH = sizeof(R) == 4 ? 12 : 13;
+// Fast path of hpsi_one (NT = 512, E = EPT * 512): compile-time element
+// offsets, the sign as a bit flip of the coefficient.
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ void hpsi_fast(Cx<R> *acc, const Cx<R> *t, uint32_t X, uint32_t sm, R g) {
+    const uint32_t xl = X & 511u, xh = X >> 9;
+    const Cx<R> *tb = t + (threadIdx.x ^ xl);
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
-        const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
-        const bool neg = (__popc((unsigned)(j & W)) & 1) != 0;
-        if (ODD) {
-            if (neg) { acc[j].x += g * v.y; acc[j].y -= g * v.x; }
-            else { acc[j].x -= g * v.y; acc[j].y += g * v.x; }
-        } else {
-            if (neg) { acc[j].x -= g * v.x; acc[j].y -= g * v.y; }
-            else { acc[j].x += g * v.x; acc[j].y += g * v.y; }
+        const Cx<R> v = tb[((uint32_t)j ^ xh) << 9];
+        R f;
+        switch (j) {
+#define SV_FB(J) case J: f = flip_bit<J>(g, sm); break;
+            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
+            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
+#undef SV_FB
+        default: f = g; break;
         }
-    }
-}
-
-template <typename R, int EPT>
-__device__ __forceinline__ void hpsi_static_dispatch(Cx<R> *acc, const unsigned char *tbytes, uint32_t B, R g,
-                                                     uint32_t w, bool odd) {
-    const uint32_t key = (w & (uint32_t)(EPT - 1)) | (odd ? 16u : 0u);
-    switch (key) {
-#define SV_HS(W)                                                               \
-    case W: hpsi_static<R, EPT, W, false>(acc, tbytes, B, g); break;           \
-    case W + 16: hpsi_static<R, EPT, W, true>(acc, tbytes, B, g); break;
-        SV_HS(0) SV_HS(1) SV_HS(2) SV_HS(3) SV_HS(4) SV_HS(5) SV_HS(6) SV_HS(7)
-        SV_HS(8) SV_HS(9) SV_HS(10) SV_HS(11) SV_HS(12) SV_HS(13) SV_HS(14) SV_HS(15)
-#undef SV_HS
-    default: break;
+        if (ODD) {
+            acc[j].x -= f * v.y;
+            acc[j].y += f * v.x;
+        } else {
+            acc[j].x += f * v.x;
+            acc[j].y += f * v.y;
+        }
     }
 }
 
@@ -1357,8 +1426,6 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
         const uint64_t ci = blockIdx.x + it * gridDim.x;
         const uint64_t rep = deposit(ci, a.freeb, a.nfree);
         Cx<R> *t = buf + (it & 1) * E;
-        // the coset's previous lambda is loaded into registers while the
-        // strings are applied
         Cx<R> acc[EPT], old[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
@@ -1371,20 +1438,16 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
         __syncthreads();
         for (int gi = a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
-            const uint32_t B = (threadIdx.x ^ G.X) * (uint32_t)sizeof(Cx<R>);
             for (int s = G.s_begin; s < G.s_end; ++s) {
                 const DevString S = strs[s];
                 const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
-                if (fast) {
-                    R g = sizeof(R) == 4 ? (R)S.coef_f : ((S.nY & 2) ? -(R)S.coef : (R)S.coef);
-                    g = base ? -g : g;
-                    hpsi_static_dispatch<R, EPT>(acc, reinterpret_cast<const unsigned char *>(t), B, g,
-                                                 S.bz >> tc.ash, (S.nY & 1) != 0);
-                    continue;
-                }
                 const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                 const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
-                if (S.nY & 1) {
+                if (fast) {
+                    const uint32_t sm = base ? ~jm : jm;
+                    if (S.nY & 1) hpsi_fast<R, EPT, true>(acc, t, G.X, sm, g);
+                    else hpsi_fast<R, EPT, false>(acc, t, G.X, sm, g);
+                } else if (S.nY & 1) {
                     hpsi_one<R, EPT, true>(acc, t, G.X, base, jm, g, E);
                 } else {
                     hpsi_one<R, EPT, false>(acc, t, G.X, base, jm, g, E);
@@ -1764,7 +1827,7 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
 template <typename R>
 cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePassArgs &a, const DevOp *ops,
                               const Phase *phases, const void *coef, const void *mats) {
-    const size_t sm = ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
+    const size_t sm = 2 * ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
                       (size_t)(a.op_end - a.op_begin) * sizeof(StagedOp<R>) + 64;
     switch (a.k - 9) {
 #define SV_GR(RB)                                                                                            \
@@ -1785,14 +1848,24 @@ template <typename R>
 cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
                              const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
                              int part_stride) {
-    const size_t sm = 2 * ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
-                      (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) + 64;
+    const size_t tile = ((size_t)1 << a.k) * sizeof(Cx<R>);
+    const size_t rest = ((size_t)1 << (a.k - a.nlow)) * 8 + (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) + 64;
+    const bool pref = 3 * tile + rest <= (size_t)227 * 1024;
+    const size_t sm = (pref ? 3 : 2) * tile + rest;
     switch (a.k - 9) {
 #define SV_AR(RB)                                                                                            \
     case RB:                                                                                                 \
-        allow_smem(k_adj_reg<R, RB>, sm);                                                                    \
-        k_adj_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases, (const R *)coef, \
-                                                (const Cx<R> *)mats, part, part_stride);                     \
+        if (pref) {                                                                                          \
+            allow_smem(k_adj_reg<R, RB, true>, sm);                                                          \
+            k_adj_reg<R, RB, true><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases,        \
+                                                          (const R *)coef, (const Cx<R> *)mats, part,        \
+                                                          part_stride);                                      \
+        } else {                                                                                             \
+            allow_smem(k_adj_reg<R, RB, false>, sm);                                                         \
+            k_adj_reg<R, RB, false><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases,       \
+                                                           (const R *)coef, (const Cx<R> *)mats, part,       \
+                                                           part_stride);                                     \
+        }                                                                                                    \
         break;
         SV_AR(2) SV_AR(3) SV_AR(4)
 #undef SV_AR
@@ -1877,7 +1950,7 @@ cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const
     for (int b = 0; b < n; ++b)
         if (!(inside >> b & 1)) a.out[a.nout++] = (int8_t)b;
     const size_t es = dt == SV_C64 ? 8 : 16;
-    const size_t sm = 2 * ((size_t)1 << a.ntb) * es + ((size_t)1 << (a.ntb - a.L)) * 8;
+    const size_t sm = 2 * ((size_t)1 << a.ntb) * es + ((size_t)1 << (a.ntb - a.L)) * 8 + ((size_t)1 << a.ntb) * 2;
     const int threads = 256;
     int grid;
     if (dt == SV_C64) {
@@ -1908,8 +1981,9 @@ cudaError_t evc_dispatch(cudaStream_t st, int grid, const void *psi, const Coset
                            (size_t)kEvcFew * threads * (sizeof(R) + 4);
 #define SV_EVCF_CASE(N)                                                                                      \
     case N:                                                                                                  \
-        allow_smem(k_evc_few<R, N>, smf);                                                                    \
-        k_evc_few<R, N><<<grid, threads, smf, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride); \
+        allow_smem(k_evc_few<R, N, 9>, smf);                                                                 \
+        k_evc_few<R, N, 9><<<grid, threads, smf, st>>>((const Cx<R> *)psi, a, groups, strs, part,            \
+                                                      part_stride);                                          \
         return cudaGetLastError();
         switch (ept) {
             SV_EVCF_CASE(1)

@@ -39,8 +39,6 @@ struct DevString {
     double coef;
     int32_t nY;
     uint32_t bz;      // parities of the pass's span basis against z
-    float coef_f;     // coef with the sign of i^nY's real factor ((nY & 2) ? -coef : coef), as float
-    int32_t pad;
 };
 
 // Batched kernel arguments (see K-BATCH in kernels.cu).

@@ -117,8 +117,6 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
         ss[i].coef = P.strings[i].coef;
         ss[i].nY = P.strings[i].nY;
         ss[i].bz = P.strings[i].bz;
-        ss[i].coef_f = (float)((P.strings[i].nY & 2) ? -P.strings[i].coef : P.strings[i].coef);
-        ss[i].pad = 0;
     }
 
     // carve the array: tables, results, then per-CTA partial rows
