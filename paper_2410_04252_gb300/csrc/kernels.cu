@@ -661,6 +661,65 @@ __device__ __forceinline__ void stage_ops(StagedOp<R> *so, const DevOp *ops, int
     }
 }
 
+// ---- diagonal blocks (see DiagBlock): per launch, every thread builds its
+// thread factor C and CZ sign pattern M for each block of the pass, and the
+// first 2^RB threads the register table Rt; adj builds the tables of D^dagger.
+__device__ __forceinline__ uint32_t reg_bit_pattern(int a) {   // v in [0, 16) with bit a set
+    return a == 0 ? 0xAAAAu : a == 1 ? 0xCCCCu : a == 2 ? 0xF0F0u : 0xFF00u;
+}
+
+template <typename R, int RB>
+__device__ void diag_setup(const GatePassArgs &a, const DiagBlock *__restrict__ blocks,
+                           const DiagMember *__restrict__ mem, const StagedOp<R> *so, Cx<R> *Rt, Cx<R> *C,
+                           uint16_t *M, bool adj) {
+    constexpr int V = 1 << RB;
+    const int NT = blockDim.x;
+    for (int lb = 0; lb < a.db_end - a.db_begin; ++lb) {
+        const DiagBlock B = blocks[a.db_begin + lb];
+        uint32_t base, sp[V];
+        phase_index<RB>(B.rmask, a.k, base, sp);
+        Cx<R> w = mk<R>(1, 0);
+        uint32_t msk = 0;
+        const int v = threadIdx.x;
+        Cx<R> r = mk<R>(1, 0);
+        for (int mi = B.m_begin; mi < B.m_end; ++mi) {
+            const DiagMember m = mem[mi];
+            const StagedOp<R> o = so[m.op - a.op_begin];
+            const R sgn = adj ? -o.s : o.s;
+            switch (m.type) {
+            case SV_DM_THR_RZ: w = cmul<R>(w, mk<R>(o.c, ((base >> m.a) & 1u) ? sgn : -sgn)); break;
+            case SV_DM_THR_CZ: if ((base >> m.a) & (base >> m.b) & 1u) w = mk<R>(-w.x, -w.y); break;
+            case SV_DM_MIX_CZ: if ((base >> m.b) & 1u) msk ^= reg_bit_pattern(m.a); break;
+            case SV_DM_REG_RZ: r = cmul<R>(r, mk<R>(o.c, ((v >> m.a) & 1) ? sgn : -sgn)); break;
+            case SV_DM_REG_CZ: if ((v >> m.a) & (v >> m.b) & 1) r = mk<R>(-r.x, -r.y); break;
+            default: break;
+            }
+        }
+        C[lb * NT + threadIdx.x] = w;
+        M[lb * NT + threadIdx.x] = (uint16_t)msk;
+        if (threadIdx.x < V) Rt[lb * 16 + threadIdx.x] = r;
+    }
+}
+
+// x[v] *= C * Rt[v] * (-1)^{M_v}
+template <typename R, int RB>
+__device__ __forceinline__ void diag_apply(Cx<R> *x, int lb, const Cx<R> *Rt, const Cx<R> *C, const uint16_t *M) {
+    constexpr int V = 1 << RB;
+    const Cx<R> c = C[lb * blockDim.x + threadIdx.x];
+    const uint32_t msk = M[lb * blockDim.x + threadIdx.x];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        Cx<R> w = cmul<R>(c, Rt[lb * 16 + v]);
+        if ((msk >> v) & 1u) w = mk<R>(-w.x, -w.y);
+        x[v] = cmul<R>(x[v], w);
+    }
+}
+
+// Hint: bring [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte aligned).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // One amplitude (8 or 16 bytes) copied global -> shared asynchronously.
 template <typename R>
 __device__ __forceinline__ void cp_async_amp(Cx<R> *dst, const Cx<R> *src) {
@@ -682,16 +741,24 @@ __device__ __forceinline__ void load_tile_async(Cx<R> *tile, const Cx<R> *psi, u
 template <typename R, int RB>
 __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, const GatePassArgs a,
                                                      const DevOp *__restrict__ ops, const Phase *__restrict__ phases,
-                                                     const R *__restrict__ coef, const Cx<R> *__restrict__ mats) {
+                                                     const R *__restrict__ coef, const Cx<R> *__restrict__ mats,
+                                                     const DiagBlock *__restrict__ dblocks,
+                                                     const DiagMember *__restrict__ dmem) {
     constexpr int V = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t T = 1u << a.k;
     const uint32_t nh = 1u << (a.k - a.nlow);
+    const int nb = a.db_end - a.db_begin;
     Cx<R> *tiles = reinterpret_cast<Cx<R> *>(smem);          // two tiles: the next one streams in
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(tiles + 2 * T);
+    Cx<R> *dC = tiles + 2 * T;                                // [nb][NT] diagonal-block thread factors
+    Cx<R> *dR = dC + nb * blockDim.x;                         // [nb][16] register tables
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(dR + nb * 16);
     StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(hioff + nh);
+    uint16_t *dM = reinterpret_cast<uint16_t *>(so + (a.op_end - a.op_begin));   // [nb][NT] CZ sign patterns
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
     stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
+    __syncthreads();
+    diag_setup<R, RB>(a, dblocks, dmem, so, dR, dC, dM, false);
     __syncthreads();
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
@@ -714,12 +781,19 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
             Cx<R> x[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
-            for (int o = P.op_begin; o < P.op_end; ++o) {
+            for (int o = P.op_begin; o < P.op_end;) {
                 const StagedOp<R> x_op = so[o - a.op_begin];
                 DevOp op = x_op.op;
+                if (op.mat <= -2) {                  // a diagonal block: all its members at once
+                    const int bi = -2 - op.mat;
+                    diag_apply<R, RB>(x, bi - a.db_begin, dR, dC, dM);
+                    o = dblocks[bi].op_end;
+                    continue;
+                }
                 const R cs[2] = {x_op.c, x_op.s};
                 op.gate = 0;
                 reg_apply<R, RB>(x, op, P.rmask, base, cs, mats, false);
+                ++o;
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) tile[swz_tile(base | sp[v])] = x[v];
@@ -738,7 +812,8 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                                                     const GatePassArgs a, const DevOp *__restrict__ ops,
                                                     const Phase *__restrict__ phases, const R *__restrict__ coef,
                                                     const Cx<R> *__restrict__ mats, double *__restrict__ part,
-                                                    int part_stride) {
+                                                    int part_stride, const DiagBlock *__restrict__ dblocks,
+                                                    const DiagMember *__restrict__ dmem) {
     constexpr int V = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t T = 1u << a.k;
@@ -747,14 +822,20 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // shared memory: lambda tile, then psi tiles (two when PREF: the next
     // tile's psi streams in while the current one is processed)
+    const int nb = a.db_end - a.db_begin;
     Cx<R> *tl = reinterpret_cast<Cx<R> *>(smem);
     Cx<R> *tps = tl + T;
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(tps + (PREF ? 2 : 1) * T);
+    Cx<R> *dC = tps + (PREF ? 2 : 1) * T;                     // [nb][NT] diagonal-block thread factors (of D^dagger)
+    Cx<R> *dR = dC + nb * blockDim.x;                         // [nb][16] register tables
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(dR + nb * 16);
     double *acc = reinterpret_cast<double *>(hioff + nh);
     StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(acc + nops * nwarps);
+    uint16_t *dM = reinterpret_cast<uint16_t *>(so + nops);                       // [nb][NT] CZ sign patterns
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
     for (int j = threadIdx.x; j < nops * nwarps; j += blockDim.x) acc[j] = 0.0;
     stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
+    __syncthreads();
+    diag_setup<R, RB>(a, dblocks, dmem, so, dR, dC, dM, true);
     __syncthreads();
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
@@ -767,6 +848,15 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
         const uint64_t ti = blockIdx.x + it * gridDim.x;
         const uint64_t gbase = deposit(ti, a.out, a.nout);
         Cx<R> *tp = tps + (PREF ? (it & 1) * T : 0);
+        if (!PREF && it + 1 < mine) {
+            // the next tile's psi and lambda runs head for L2 while this one is processed
+            const uint64_t gn = deposit(ti + gridDim.x, a.out, a.nout);
+            const uint32_t runbytes = (1u << a.nlow) * (uint32_t)sizeof(Cx<R>);
+            for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) {
+                prefetch_l2(psi + (gn | hioff[j]), runbytes);
+                prefetch_l2(lam + (gn | hioff[j]), runbytes);
+            }
+        }
         if (PREF) {
             if (it + 1 < mine)
                 load_tile_async<R>(tps + ((it + 1) & 1) * T, psi, deposit(ti + gridDim.x, a.out, a.nout), hioff,
@@ -791,9 +881,49 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                 xp[v] = tp[si];
                 xl[v] = tl[si];
             }
-            for (int o = P.op_end - 1; o >= P.op_begin; --o) {
+            for (int o = P.op_end - 1; o >= P.op_begin;) {
                 const StagedOp<R> x_op = so[o - a.op_begin];
                 DevOp op = x_op.op;
+                if (op.mat <= -2) {
+                    // a diagonal block: every member's generator expectation
+                    // at the block's end (Z commutes with the block), then
+                    // D^dagger on both register sets
+                    const int bi = -2 - op.mat;
+                    const DiagBlock B = dblocks[bi];
+                    R tv[V], tot = 0;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        tv[v] = xl[v].x * xp[v].y - xl[v].y * xp[v].x;
+                        tot += tv[v];
+                    }
+                    R sb[RB];
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) {
+                        R acc_b = 0;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc_b += ((v >> b) & 1) ? -tv[v] : tv[v];
+                        sb[b] = acc_b;
+                    }
+                    for (int mi = B.m_begin; mi < B.m_end; ++mi) {
+                        const DiagMember m = dmem[mi];
+                        R g;
+                        if (m.type == SV_DM_REG_RZ) {
+                            g = sb[0];
+#pragma unroll
+                            for (int b = 1; b < RB; ++b) g = (m.a == b) ? sb[b] : g;
+                        } else if (m.type == SV_DM_THR_RZ) {
+                            g = ((base >> m.a) & 1u) ? -tot : tot;
+                        } else {
+                            continue;
+                        }
+                        g = warp_sum<R>(g);
+                        if (lane == 0) acc[(m.op - a.op_begin) * nwarps + warp] += (double)g;
+                    }
+                    diag_apply<R, RB>(xp, bi - a.db_begin, dR, dC, dM);
+                    diag_apply<R, RB>(xl, bi - a.db_begin, dR, dC, dM);
+                    o = B.op_begin - 1;
+                    continue;
+                }
                 const R cs[2] = {x_op.c, x_op.s};
                 op.gate = 0;
                 R g = reg_adjoint<R, RB>(xp, xl, op, P.rmask, base, cs, mats);
@@ -801,6 +931,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     g = warp_sum<R>(g);
                     if (lane == 0) acc[(o - a.op_begin) * nwarps + warp] += (double)g;
                 }
+                --o;
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -1826,15 +1957,18 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
 
 template <typename R>
 cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePassArgs &a, const DevOp *ops,
-                              const Phase *phases, const void *coef, const void *mats) {
+                              const Phase *phases, const void *coef, const void *mats, const DiagBlock *dblocks,
+                              const DiagMember *dmem) {
+    const size_t nb = (size_t)(a.db_end - a.db_begin);
     const size_t sm = 2 * ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
+                      nb * (512 + 16) * sizeof(Cx<R>) + nb * 512 * 2 +
                       (size_t)(a.op_end - a.op_begin) * sizeof(StagedOp<R>) + 64;
     switch (a.k - 9) {
 #define SV_GR(RB)                                                                                            \
     case RB:                                                                                                 \
         allow_smem(k_gate_reg<R, RB>, sm);                                                                   \
         k_gate_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, a, ops, phases, (const R *)coef,              \
-                                                 (const Cx<R> *)mats);                                       \
+                                                 (const Cx<R> *)mats, dblocks, dmem);                        \
         break;
         SV_GR(2) SV_GR(3) SV_GR(4)
 #undef SV_GR
@@ -1847,10 +1981,13 @@ cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePa
 template <typename R>
 cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
                              const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
-                             int part_stride) {
+                             int part_stride, const DiagBlock *dblocks, const DiagMember *dmem) {
     const size_t tile = ((size_t)1 << a.k) * sizeof(Cx<R>);
-    const size_t rest = ((size_t)1 << (a.k - a.nlow)) * 8 + (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) + 64;
-    const bool pref = 3 * tile + rest <= (size_t)227 * 1024;
+    const size_t nb = (size_t)(a.db_end - a.db_begin);
+    const size_t rest = ((size_t)1 << (a.k - a.nlow)) * 8 + (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) +
+                        nb * (512 + 16) * sizeof(Cx<R>) + nb * 512 * 2 + 64;
+    const bool pref = false;   // measured slower than loading psi and lambda together
+    (void)pref;
     const size_t sm = (pref ? 3 : 2) * tile + rest;
     switch (a.k - 9) {
 #define SV_AR(RB)                                                                                            \
@@ -1859,12 +1996,12 @@ cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, co
             allow_smem(k_adj_reg<R, RB, true>, sm);                                                          \
             k_adj_reg<R, RB, true><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases,        \
                                                           (const R *)coef, (const Cx<R> *)mats, part,        \
-                                                          part_stride);                                      \
+                                                          part_stride, dblocks, dmem);                       \
         } else {                                                                                             \
             allow_smem(k_adj_reg<R, RB, false>, sm);                                                         \
             k_adj_reg<R, RB, false><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases,       \
                                                            (const R *)coef, (const Cx<R> *)mats, part,       \
-                                                           part_stride);                                     \
+                                                           part_stride, dblocks, dmem);                      \
         }                                                                                                    \
         break;
         SV_AR(2) SV_AR(3) SV_AR(4)
@@ -1876,16 +2013,18 @@ cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, co
 }
 
 cudaError_t launch_gate_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, const GatePassArgs &a,
-                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats) {
-    if (dt == SV_C64) return gate_reg_dispatch<float>(st, grid, psi, a, ops, phases, coef, mats);
-    return gate_reg_dispatch<double>(st, grid, psi, a, ops, phases, coef, mats);
+                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats,
+                            const DiagBlock *dblocks, const DiagMember *dmem) {
+    if (dt == SV_C64) return gate_reg_dispatch<float>(st, grid, psi, a, ops, phases, coef, mats, dblocks, dmem);
+    return gate_reg_dispatch<double>(st, grid, psi, a, ops, phases, coef, mats, dblocks, dmem);
 }
 
 cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
-                           int part_stride) {
-    if (dt == SV_C64) return adj_reg_dispatch<float>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride);
-    return adj_reg_dispatch<double>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride);
+                           int part_stride, const DiagBlock *dblocks, const DiagMember *dmem) {
+    if (dt == SV_C64)
+        return adj_reg_dispatch<float>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride, dblocks, dmem);
+    return adj_reg_dispatch<double>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride, dblocks, dmem);
 }
 
 cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi, void *lam,

@@ -14,6 +14,7 @@ namespace sv {
 struct GatePassArgs {
     int n, k, nlow, nhi, nout, op_begin, op_end;
     int ph_begin, ph_end;    // register phases (register-blocked pass), else -1
+    int db_begin, db_end;    // diagonal blocks of the pass
     int8_t hi[40];
     int8_t out[64];
 };
@@ -82,10 +83,11 @@ cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads,
                             double *part, int part_stride);
 // Register-blocked passes (512 threads; a.ph_begin >= 0, 11 <= k <= 13).
 cudaError_t launch_gate_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, const GatePassArgs &a,
-                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats);
+                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats,
+                            const DiagBlock *dblocks, const DiagMember *dmem);
 cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
-                           int part_stride);
+                           int part_stride, const DiagBlock *dblocks, const DiagMember *dmem);
 // In-place swap of disjoint physical bit pairs (pairs[2i], pairs[2i+1]).
 cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const int32_t *pairs,
                            int npairs, int blocks_per_sm);

@@ -408,6 +408,100 @@ void plan_phases(QsuPlan &P) {
     }
 }
 
+// Diagonal blocks: inside each register phase, every run of >= 2
+// consecutive RZ / CZ operations becomes one block (they commute, so the run
+// is one diagonal operator; in the adjoint sweep every member's generator
+// expectation is taken at the run's end, since Z commutes with the run).
+// Inside a phase, diagonal operations are delayed past later non-diagonal
+// operations on other qubits (disjoint supports commute, diagonal operations
+// commute with each other), so that they gather into long runs; a
+// non-diagonal operation that shares a qubit with a delayed diagonal one
+// first flushes the delayed ones.  The order stays a valid schedule (C1).
+void cluster_diagonals(QsuPlan &P, const Phase &F) {
+    auto tm = [](const DevOp &d) {
+        uint32_t m = 1u << d.t[0];
+        if (d.kind == SV_CZ) m |= 1u << d.t[1];
+        return m;
+    };
+    std::vector<DevOp> out, pend;
+    uint32_t pmask = 0;
+    for (int o = F.op_begin; o < F.op_end; ++o) {
+        const DevOp &d = P.ops[o];
+        if (diag_kind(d.kind)) {
+            pend.push_back(d);
+            pmask |= tm(d);
+            continue;
+        }
+        if (tm(d) & pmask) {
+            out.insert(out.end(), pend.begin(), pend.end());
+            pend.clear();
+            pmask = 0;
+        }
+        out.push_back(d);
+    }
+    out.insert(out.end(), pend.begin(), pend.end());
+    std::copy(out.begin(), out.end(), P.ops.begin() + F.op_begin);
+}
+
+// A run is worth a block when its members cost more than one block
+// application (about two complex products per amplitude): RZ ~ one complex
+// product per amplitude, CZ ~ a quarter.
+bool diag_run_pays(const QsuPlan &P, int o, int e) {
+    int rz = 0, cz = 0;
+    for (int u = o; u < e; ++u) (P.ops[u].kind == SV_RZ ? rz : cz)++;
+    return 4 * rz + cz > 10;
+}
+
+void plan_diag_blocks(QsuPlan &P, int max_diag) {
+    for (auto &gp : P.passes) {
+        gp.db_begin = gp.db_end = (int32_t)P.dblocks.size();
+        if (gp.ph_begin < 0) continue;
+        for (int ph = gp.ph_begin; ph < gp.ph_end; ++ph) {
+            const Phase &F = P.phases[ph];
+            cluster_diagonals(P, F);
+            int o = F.op_begin;
+            while (o < F.op_end) {
+                if (!diag_kind(P.ops[o].kind)) { ++o; continue; }
+                int e = o;
+                while (e < F.op_end && diag_kind(P.ops[e].kind)) ++e;
+                if (diag_run_pays(P, o, e) && (int)P.dblocks.size() - gp.db_begin < max_diag) {
+                    DiagBlock B;
+                    B.op_begin = o;
+                    B.op_end = e;
+                    B.m_begin = (int32_t)P.dmembers.size();
+                    B.rmask = F.rmask;
+                    B.pad = 0;
+                    const int bi = (int)P.dblocks.size();
+                    auto regidx = [&](int t) { return __builtin_popcount(F.rmask & ((1u << t) - 1u)); };
+                    for (int u = o; u < e; ++u) {
+                        DevOp &d = P.ops[u];
+                        DiagMember m;
+                        m.op = u;
+                        m.a = m.b = 0;
+                        if (d.kind == SV_RZ) {
+                            const int t = d.t[0];
+                            if (F.rmask >> t & 1u) { m.type = SV_DM_REG_RZ; m.a = regidx(t); }
+                            else { m.type = SV_DM_THR_RZ; m.a = t; }
+                        } else {
+                            const int t0 = d.t[0], t1 = d.t[1];
+                            const bool r0 = F.rmask >> t0 & 1u, r1 = F.rmask >> t1 & 1u;
+                            if (r0 && r1) { m.type = SV_DM_REG_CZ; m.a = regidx(t0); m.b = regidx(t1); }
+                            else if (!r0 && !r1) { m.type = SV_DM_THR_CZ; m.a = t0; m.b = t1; }
+                            else { m.type = SV_DM_MIX_CZ; m.a = regidx(r0 ? t0 : t1); m.b = r0 ? t1 : t0; }
+                        }
+                        d.mat = -2 - bi;
+                        P.dmembers.push_back(m);
+                    }
+                    B.m_end = (int32_t)P.dmembers.size();
+                    P.dblocks.push_back(B);
+                }
+                o = e;
+            }
+        }
+        gp.db_end = (int32_t)P.dblocks.size();
+    }
+}
+
 // ---------------------------------------------------------- coset passes --
 // Strings sharing a physical X/Y mask x form a group: one read of psi serves
 // all of them.  A pass stages 2^(kl+m) amplitudes: the 2^m runs of 2^kl
@@ -784,6 +878,7 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
     int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
     plan_gate_passes(P, ops, k, o.low_bits, o.fuse_max);
     plan_phases(P);
+    plan_diag_blocks(P, std::min(o.max_diag, kMaxPassDiag));
     return "";
 }
 

@@ -50,7 +50,28 @@ struct GatePass {
     uint64_t bits = 0;                // physical staged bits
     int32_t op_begin = 0, op_end = 0; // into QsuPlan::ops
     int32_t ph_begin = -1, ph_end = -1;  // register phases (register-blocked passes), else -1
+    int32_t db_begin = 0, db_end = 0;    // diagonal blocks of the pass (register-blocked passes)
 };
+
+// A run of consecutive diagonal operations (RZ, CZ) inside one register
+// phase, applied as one diagonal operator: the phase factor of a register
+// amplitude is a thread constant (operations on thread bits) times a table
+// entry indexed by the register bits (operations on register bits), with a
+// per-thread sign pattern for CZs between a register and a thread bit.
+// Every member op carries mat = -2 - (block index).
+struct DiagBlock {
+    int32_t op_begin, op_end;     // member ops (consecutive in QsuPlan::ops)
+    int32_t m_begin, m_end;       // into QsuPlan::dmembers
+    uint32_t rmask;               // register tile bits of the phase
+    int32_t pad;
+};
+enum { SV_DM_REG_RZ = 0, SV_DM_THR_RZ = 1, SV_DM_REG_CZ = 2, SV_DM_THR_CZ = 3, SV_DM_MIX_CZ = 4 };
+struct DiagMember {
+    int32_t type;     // SV_DM_*
+    int32_t a, b;     // register index (0..r-1) or tile bit, per type; MIX_CZ: a register, b tile bit
+    int32_t op;       // index into QsuPlan::ops (coefficient and gradient slot)
+};
+constexpr int kMaxPassDiag = 10;       // diagonal blocks per register-blocked pass
 
 // A register phase of a register-blocked pass: each thread holds the
 // amplitudes spanned by the tile bits in rmask; ops [op_begin, op_end) are
@@ -69,6 +90,8 @@ struct QsuPlan {
     std::vector<GatePass> passes;
     std::vector<DevOp> ops;           // pass operations, pass by pass, in execution order
     std::vector<Phase> phases;        // register phases of register-blocked passes
+    std::vector<DiagBlock> dblocks;   // diagonal blocks of register phases
+    std::vector<DiagMember> dmembers;
     std::vector<int32_t> init_l2p, final_l2p;
     int32_t nqr() const {
         int32_t c = 0;
@@ -122,6 +145,7 @@ struct PlanOptions {
     bool pad_highest = true;
     int fuse_max = 0;            // gate operations per gate pass (0 = as many as fit)
     int hier_intra = -1;         // >= 0: hierarchical tiling (Alg. 4/5) with this many intra qubits
+    int max_diag = kMaxPassDiag; // diagonal blocks per register-blocked pass (shared-memory budget)
 };
 
 // Returns an empty string on success, else the error message.

@@ -317,3 +317,28 @@ def test_hierarchical_schedule(ni):
     e, gr = s.grad(c, p, h, sv.HIER)
     assert abs(e - ograd.objective(c, p, h, init)) < 1e-4 * l1(h)
     assert np.max(np.abs(gr - ograd.finite_difference(c, p, h, init))) < 1e-4 * l1(h)
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("fuse_max", [0, 20])
+def test_register_passes_full_tiles(dtype, fuse_max):
+    """HEA with the largest staged tiles (k = 13 for complex64, 12 for
+    complex128: 16 / 8 amplitudes per thread in the register phases, with
+    diagonal blocks of RZ / CZ runs): state, energy and gradient against the
+    oracle; fuse_max = 20 cuts the passes so that blocks start and end
+    inside phases differently."""
+    n, g = 16, 2
+    c = W.hea_circuit(n, 3)
+    p = W.uniform_params(c.nparams, 141, 0, 2 * math.pi)
+    o = sv.default_options(dtype)
+    o.fuse_max = fuse_max
+    s = sv.StateVector(n, g, dtype, options=o)
+    s.reset(0)
+    s.apply_circuit(c, p, sv.LAZY)
+    ref = oracle_state(c, p, 0)
+    assert np.max(np.abs(s.get_state() - ref)) < AMP_TOL[dtype]
+    h = W.random_hamiltonian(n, 40, 142)
+    e, gr, _ = s.vqe_step(0, c, p, h, sv.LAZY)
+    tol = 1e-4 * l1(h) if dtype == sv.C64 else 1e-10 * l1(h)
+    assert abs(e - ograd.objective(c, p, h)) < tol
+    assert np.max(np.abs(gr - ograd.parameter_shift(c, p, h))) < tol
