@@ -1150,12 +1150,14 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     o.evc_span = std::min(d.evc_span, o.tile_bits - o.evc_low_bits);
     const int kmax = o.tile_bits;
     const int hio = std::max(8, kmax - o.low_bits);
-    const PlanOptions po = plan_options(o);
+    PlanOptions po = plan_options(o);
+    po.max_diag = 0;                     // the batched kernel applies RZ / CZ one by one
     std::vector<int32_t> l2p(n);
     for (int q = 0; q < n; ++q) l2p[q] = q;
     // one plan per distinct circuit
     std::vector<int32_t> state_plan(batch), plan_pass_off{0}, plan_op_off{0}, gparam;
     std::vector<GatePassArgs> passes;
+    std::vector<Phase> phases;
     std::vector<DevOp> ops;
     std::vector<uint64_t> plan_keys;
     std::vector<int32_t> gsize(batch);
@@ -1185,11 +1187,22 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
             if (!err.empty()) return fail(SV_EINVAL, "state " + std::to_string(b) + ": " + err);
             if ((int)P.ops.size() > batch_max_ops()) return fail(SV_EINVAL, "sv_batch_run: more than 512 gates in a state");
             const int obase = (int)ops.size();
+            const int pbase = (int)phases.size();
             for (auto &gp : P.passes) {
                 GatePassArgs a = gate_args(n, gp);
                 a.op_begin += obase;
                 a.op_end += obase;
+                if (a.ph_begin >= 0) {
+                    a.ph_begin += pbase;
+                    a.ph_end += pbase;
+                }
+                a.db_begin = a.db_end = 0;
                 passes.push_back(a);
+            }
+            for (Phase f : P.phases) {
+                f.op_begin += obase;
+                f.op_end += obase;
+                phases.push_back(f);
             }
             ops.insert(ops.end(), P.ops.begin(), P.ops.end());
             plan_pass_off.push_back((int32_t)passes.size());
@@ -1230,7 +1243,7 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     if (occ < 1) return fail(SV_EINVAL, "sv_batch_run: the batched kernel does not fit an SM with these options");
     const int grid = std::min(batch, device_sms() * occ);
     const size_t es = dt == SV_C64 ? 8 : 16;
-    std::vector<DevBuf> bufs(16);
+    std::vector<DevBuf> bufs(17);
     auto up = [&](int i, const void *src, size_t bytes) -> cudaError_t {
         cudaError_t e = bufs[i].ensure(std::max<size_t>(bytes, 16));
         if (e != cudaSuccess || !bytes) return e;
@@ -1262,6 +1275,7 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     SV_BCK(up(10, hp.data(), hp.size() * sizeof(CosetArgs)));
     SV_BCK(up(11, gs.data(), gs.size() * sizeof(DevGroup)));
     SV_BCK(up(12, ss.data(), ss.size() * sizeof(DevString)));
+    SV_BCK(up(16, phases.data(), phases.size() * sizeof(Phase)));
     SV_BCK(bufs[13].ensure((size_t)grid * 2 * ((size_t)1 << n) * es));
     SV_BCK(bufs[14].ensure((batch + nparams + 2 * (size_t)batch) * 8 + 64));
     double *d_energy = bufs[14].as<double>();
@@ -1277,6 +1291,7 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     a.hio = hio;
     a.init_index = init_index;
     a.passes = bufs[0].as<GatePassArgs>();
+    a.phases = bufs[16].as<Phase>();
     a.plan_pass_off = bufs[1].as<int32_t>();
     a.ops = bufs[2].as<DevOp>();
     a.plan_op_off = bufs[3].as<int32_t>();

@@ -1633,6 +1633,61 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// Register-phased tile of a gate pass inside the batched kernel (512
+// threads): the tile is staged swizzled, each phase gathers the thread's
+// 2^RB amplitudes, applies its gates in registers, scatters them back.
+template <typename R, int RB>
+__device__ __noinline__ void batch_reg_forward(Cx<R> *tile, const GatePassArgs &P, const DevOp *ops, const Phase *phases,
+                                  const R *coef) {
+    constexpr int V = 1 << RB;
+    for (int ph = P.ph_begin; ph < P.ph_end; ++ph) {
+        const Phase F = phases[ph];
+        uint32_t base, sp[V];
+        phase_index<RB>(F.rmask, P.k, base, sp);
+        Cx<R> x[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
+        for (int o = F.op_begin; o < F.op_end; ++o) reg_apply<R, RB>(x, ops[o], F.rmask, base, coef, nullptr, false);
+#pragma unroll
+        for (int v = 0; v < V; ++v) tile[swz_tile(base | sp[v])] = x[v];
+        __syncthreads();
+    }
+}
+
+template <typename R, int RB>
+__device__ __noinline__ void batch_reg_adjoint(Cx<R> *tp, Cx<R> *tl, const GatePassArgs &P, const DevOp *ops,
+                                  const Phase *phases, const R *coef, double *opacc, int o0) {
+    constexpr int V = 1 << RB;
+    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ph = P.ph_end - 1; ph >= P.ph_begin; --ph) {
+        const Phase F = phases[ph];
+        uint32_t base, sp[V];
+        phase_index<RB>(F.rmask, P.k, base, sp);
+        Cx<R> xp[V], xl[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t si = swz_tile(base | sp[v]);
+            xp[v] = tp[si];
+            xl[v] = tl[si];
+        }
+        for (int o = F.op_end - 1; o >= F.op_begin; --o) {
+            const DevOp op = ops[o];
+            R g = reg_adjoint<R, RB>(xp, xl, op, F.rmask, base, coef, nullptr);
+            if (has_param(op.kind)) {
+                g = warp_sum<R>(g);
+                if (lane == 0) opacc[(o - o0) * nwarps + warp] += (double)g;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint32_t si = swz_tile(base | sp[v]);
+            tp[si] = xp[v];
+            tl[si] = xl[v];
+        }
+        __syncthreads();
+    }
+}
+
 constexpr int kBatchMaxOps = 512;      // gate operations per state (smem accumulators)
 constexpr int kBatchMaxGates = 1024;
 
@@ -1678,8 +1733,21 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
             const uint32_t T = 1u << P.k, nh = 1u << (P.k - P.nlow), lowmask = (1u << P.nlow) - 1u;
             for (uint32_t j = threadIdx.x; j < nh; j += NT) hioff[j] = deposit(j, P.hi, P.nhi);
             __syncthreads();
+            const int rb = (P.ph_begin >= 0 && NT == 512) ? P.k - 9 : 0;   // register-phased pass
             for (uint64_t ti = 0; ti < (1ull << P.nout); ++ti) {
                 const uint64_t base = deposit(ti, P.out, P.nout);
+                if (rb >= 2 && rb <= 4) {
+                    for (uint32_t j = threadIdx.x; j < T; j += NT)
+                        tp[swz_tile(j)] = psi[base | hioff[j >> P.nlow] | (j & lowmask)];
+                    __syncthreads();
+                    if (rb == 4) batch_reg_forward<R, 4>(tp, P, a.ops, a.phases, coef);
+                    else if (rb == 3) batch_reg_forward<R, 3>(tp, P, a.ops, a.phases, coef);
+                    else batch_reg_forward<R, 2>(tp, P, a.ops, a.phases, coef);
+                    for (uint32_t j = threadIdx.x; j < T; j += NT)
+                        psi[base | hioff[j >> P.nlow] | (j & lowmask)] = tp[swz_tile(j)];
+                    __syncthreads();
+                    continue;
+                }
                 for (uint32_t j = threadIdx.x; j < T; j += NT) tp[j] = psi[base | hioff[j >> P.nlow] | (j & lowmask)];
                 __syncthreads();
                 for (int o = P.op_begin; o < P.op_end; ++o) {
@@ -1754,8 +1822,27 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
             __syncthreads();
             for (uint32_t j = threadIdx.x; j < nh; j += NT) hioff[j] = deposit(j, P.hi, P.nhi);
             __syncthreads();
+            const int rb = (P.ph_begin >= 0 && NT == 512) ? P.k - 9 : 0;   // register-phased pass
             for (uint64_t ti = 0; ti < (1ull << P.nout); ++ti) {
                 const uint64_t base = deposit(ti, P.out, P.nout);
+                if (rb >= 2 && rb <= 4) {
+                    for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                        const uint64_t gi = base | hioff[j >> P.nlow] | (j & lowmask);
+                        tp[swz_tile(j)] = psi[gi];
+                        tl[swz_tile(j)] = lam[gi];
+                    }
+                    __syncthreads();
+                    if (rb == 4) batch_reg_adjoint<R, 4>(tp, tl, P, a.ops, a.phases, coef, opacc, o0);
+                    else if (rb == 3) batch_reg_adjoint<R, 3>(tp, tl, P, a.ops, a.phases, coef, opacc, o0);
+                    else batch_reg_adjoint<R, 2>(tp, tl, P, a.ops, a.phases, coef, opacc, o0);
+                    for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                        const uint64_t gi = base | hioff[j >> P.nlow] | (j & lowmask);
+                        psi[gi] = tp[swz_tile(j)];
+                        lam[gi] = tl[swz_tile(j)];
+                    }
+                    __syncthreads();
+                    continue;
+                }
                 for (uint32_t j = threadIdx.x; j < T; j += NT) {
                     const uint64_t gi = base | hioff[j >> P.nlow] | (j & lowmask);
                     tp[j] = psi[gi];

@@ -49,6 +49,7 @@ struct BatchArgs {
     int hio;                         // entries of the high-offset table: 2^hio
     uint64_t init_index;
     const GatePassArgs *passes;      // all plans' gate passes
+    const Phase *phases;             // all plans' register phases (ph_begin/ph_end of a pass index them)
     const int32_t *plan_pass_off;    // [nplans + 1]
     const DevOp *ops;                // all plans' pass operations (gate = index within the state's circuit)
     const int32_t *plan_op_off;      // [nplans + 1]: first op of each plan (ops are plan-contiguous)
