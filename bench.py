@@ -540,8 +540,24 @@ def plan_table(args):
                                                 if inter[i] != inter[i - 1] and p["tiles"][i]["pairs"])
             row["adhoc_over_flat"] = row["adhoc_qrs"] / max(row["flat_qrs"], 1)
             rows.append(row)
+    # EVC (Sec. V-B-2): Alg. 6 with diagonalization vs the index-order ad hoc
+    # rule, JW-shaped Hamiltonians of 4096 strings on 32 chunks
+    erows = []
+    for n in range(20, 37, 4):
+        h = W.jw_hamiltonian(n, 4096, 2000 + n)
+        x, z = W.pauli_masks(h)
+        row = {"n": n, "strings": len(h.coeffs)}
+        for name, sched in (("lazy", sv.LAZY), ("adhoc", sv.EAGER)):
+            t0 = time.perf_counter()
+            p = sv.plan_evc(n, g, x, z, sched)
+            row[name + "_plan_s"] = time.perf_counter() - t0
+            row[name + "_qrs"] = sum(1 for t in p["tiles"] if t["pairs"])
+        row["adhoc_over_lazy"] = row["adhoc_qrs"] / max(row["lazy_qrs"], 1)
+        erows.append(row)
     print(json.dumps({"table": "QSU QR counts, flat vs hierarchical vs ad hoc (plan level)", "g": g,
-                      "n_intra": nintra, "layers": "4n", "rows": rows}), flush=True)
+                      "n_intra": nintra, "layers": "4n", "rows": rows,
+                      "evc_table": "EVC QR counts, Alg. 6 lazy vs index-order ad hoc, JW-shaped 4096 strings",
+                      "evc_rows": erows}), flush=True)
     return 0
 
 

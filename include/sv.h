@@ -101,7 +101,9 @@ typedef struct {
     int32_t fuse_max;           /* fusion depth: at most this many gate operations per gate pass
                                    (0 = as many as fit, up to 256) */
     int32_t intra_bits;         /* SV_SCHED_HIER: intra-node global qubits n_intra, 0 <= n_intra <= g */
-    int32_t reserved;
+    int32_t plan_device;        /* where Alg. 6 searches the global sets of the lazy EVC plan: 0 = on the
+                                   GPU when C(n, g) >= 2^19 and a CUDA device is present (default), 1 = on
+                                   the GPU, 2 = on the host; both give the same plan */
 } sv_options;
 
 /* Kernel kinds counted in sv_stats. */

@@ -300,6 +300,65 @@ uint64_t qsu_key(const sv_handle *h, const sv_gate *gates, size_t m, size_t np, 
     return k;
 }
 
+// Greedy steps of Alg. 6 on the device (see k_alg6_step); buffers live for
+// one plan.
+struct Alg6Device {
+    DevBuf xs, w, binom, best;
+    cudaStream_t st = nullptr;
+    int n = -1, k = -1;
+    size_t nx = 0;
+    ~Alg6Device() {
+        if (st) cudaStreamDestroy(st);
+        xs.release(); w.release(); binom.release(); best.release();
+    }
+    std::string step(const std::vector<uint64_t> &X, const std::vector<int32_t> &W, int n_, int k_, int64_t &rank,
+                     int64_t &count) {
+        auto cuerr = [](const char *what, cudaError_t e) { return std::string(what) + ": " + cudaGetErrorString(e); };
+        cudaError_t e;
+        if (!st && (e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return cuerr("stream", e);
+        std::vector<int64_t> B((size_t)(n_ + 1) * (k_ + 1), 0);
+        for (int a = 0; a <= n_; ++a)
+            for (int b = 0; b <= k_ && b <= a; ++b) {
+                long double c = 1;
+                for (int i = 1; i <= b; ++i) c = c * (a - b + i) / i;
+                B[(size_t)a * (k_ + 1) + b] = (int64_t)(c + 0.5L);
+            }
+        const uint64_t ncand = (uint64_t)B[(size_t)n_ * (k_ + 1) + k_];
+        if (ncand >= (1ull << 32)) return "Alg. 6 search space C(n, n_G) beyond 2^32";
+        if (n_ != n || k_ != k) {
+            if ((e = upload(binom, B, st)) != cudaSuccess) return cuerr("binomials", e);
+            n = n_;
+            k = k_;
+        }
+        if (X.size() != nx) {
+            if ((e = upload(xs, X, st)) != cudaSuccess) return cuerr("supports", e);
+            nx = X.size();
+        }
+        if ((e = upload(w, W, st)) != cudaSuccess) return cuerr("weights", e);
+        if ((e = best.ensure(8)) != cudaSuccess) return cuerr("alloc", e);
+        if ((e = cudaMemsetAsync(best.p, 0, 8, st)) != cudaSuccess) return cuerr("memset", e);
+        if ((e = launch_alg6_step(st, xs.as<uint64_t>(), w.as<int32_t>(), (int)X.size(), n_, k_, binom.as<int64_t>(),
+                                  ncand, (unsigned long long *)best.p)) != cudaSuccess)
+            return cuerr("Alg. 6 kernel", e);
+        unsigned long long key = 0;
+        if ((e = cudaMemcpyAsync(&key, best.p, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return cuerr("copy", e);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuerr("sync", e);
+        count = (int64_t)(key >> 32);
+        rank = (int64_t)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+        return "";
+    }
+};
+
+bool alg6_on_device(int plan_device, int n, int g) {
+    if (plan_device == 2) return false;
+    if (plan_device == 1) return true;
+    long double c = 1;
+    for (int i = 1; i <= g; ++i) c = c * (n - g + i) / i;
+    if (c < (long double)(1 << 19)) return false;
+    int cnt = 0;
+    return cudaGetDeviceCount(&cnt) == cudaSuccess && cnt > 0;
+}
+
 sv_status check_sched(sv_schedule s) {
     if (s != SV_SCHED_EAGER && s != SV_SCHED_LAZY && s != SV_SCHED_DIRECT && s != SV_SCHED_HIER)
         return fail(SV_EINVAL, "bad schedule");
@@ -436,6 +495,10 @@ sv_status get_evc(sv_handle *h, const sv_pauli *p, const double *c, size_t nterm
     auto ent = std::make_unique<EvcEntry>();
     auto t0 = std::chrono::steady_clock::now();
     PlanOptions po = plan_options(h->opt);
+    Alg6Device a6;
+    if (!hpsi && sched != SV_SCHED_DIRECT && alg6_on_device(h->opt.plan_device, h->n, h->g))
+        po.alg6_step = [&](const std::vector<uint64_t> &X, const std::vector<int32_t> &W, int n_, int k_, int64_t &r,
+                           int64_t &c) { return a6.step(X, W, n_, k_, r, c); };
     std::string err = (hpsi || sched == SV_SCHED_DIRECT)
                           ? plan_hpsi(h->n, p, c, nterms, po, h->l2p, ent->plan)
                           : plan_evc(h->n, h->g, p, c, nterms, sched != SV_SCHED_EAGER, po, h->l2p, ent->plan);
@@ -804,6 +867,7 @@ sv_status sv_set_options(sv_handle *h, const sv_options *o) {
     if (n.threads % 32 || n.threads > 512) return fail(SV_EINVAL, "threads must be a multiple of 32, <= 512");
     if (n.fuse_max < 0) return fail(SV_EINVAL, "fuse_max must be >= 0");
     if (n.intra_bits < 0 || n.intra_bits > h->g) return fail(SV_EINVAL, "intra_bits must be in [0, g]");
+    if (n.plan_device < 0 || n.plan_device > 2) return fail(SV_EINVAL, "plan_device must be 0, 1 or 2");
     h->opt = n;
     return SV_OK;
 }
@@ -1052,10 +1116,14 @@ sv_status sv_plan_evc(int n, int g, const sv_pauli *paulis, size_t nterms, sv_sc
     auto *p = new sv_plan();
     p->kind = 1;
     SV_TRY(check_sched(sched));
+    PlanOptions po = plan_options(o);
+    Alg6Device a6;
+    if (sched != SV_SCHED_DIRECT && alg6_on_device(o.plan_device, n, g))
+        po.alg6_step = [&](const std::vector<uint64_t> &X, const std::vector<int32_t> &W, int n_, int k_, int64_t &r,
+                           int64_t &c) { return a6.step(X, W, n_, k_, r, c); };
     std::string err = sched == SV_SCHED_DIRECT
-                          ? plan_hpsi(n, paulis, ones.data(), nterms, plan_options(o), l2p, p->e)
-                          : plan_evc(n, g, paulis, ones.data(), nterms, sched != SV_SCHED_EAGER, plan_options(o), l2p,
-                                     p->e);
+                          ? plan_hpsi(n, paulis, ones.data(), nterms, po, l2p, p->e)
+                          : plan_evc(n, g, paulis, ones.data(), nterms, sched != SV_SCHED_EAGER, po, l2p, p->e);
     if (!err.empty()) {
         delete p;
         return fail(SV_EINVAL, err);

@@ -1734,20 +1734,30 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
             for (uint32_t j = threadIdx.x; j < nh; j += NT) hioff[j] = deposit(j, P.hi, P.nhi);
             __syncthreads();
             const int rb = (P.ph_begin >= 0 && NT == 512) ? P.k - 9 : 0;   // register-phased pass
-            for (uint64_t ti = 0; ti < (1ull << P.nout); ++ti) {
-                const uint64_t base = deposit(ti, P.out, P.nout);
-                if (rb >= 2 && rb <= 4) {
-                    for (uint32_t j = threadIdx.x; j < T; j += NT)
-                        tp[swz_tile(j)] = psi[base | hioff[j >> P.nlow] | (j & lowmask)];
+            const uint64_t ntl = 1ull << P.nout;
+            if (rb >= 2 && rb <= 4) {
+                // tiles alternate between the two buffers; the next one streams in
+                load_tile_async<R>(tp, psi, deposit(0, P.out, P.nout), hioff, P.nlow, T);
+                cp_async_commit();
+                for (uint64_t ti = 0; ti < ntl; ++ti) {
+                    const uint64_t base = deposit(ti, P.out, P.nout);
+                    Cx<R> *cur = (ti & 1) ? tl : tp;
+                    if (ti + 1 < ntl)
+                        load_tile_async<R>((ti & 1) ? tp : tl, psi, deposit(ti + 1, P.out, P.nout), hioff, P.nlow, T);
+                    cp_async_commit();
+                    cp_async_wait1();
                     __syncthreads();
-                    if (rb == 4) batch_reg_forward<R, 4>(tp, P, a.ops, a.phases, coef);
-                    else if (rb == 3) batch_reg_forward<R, 3>(tp, P, a.ops, a.phases, coef);
-                    else batch_reg_forward<R, 2>(tp, P, a.ops, a.phases, coef);
+                    if (rb == 4) batch_reg_forward<R, 4>(cur, P, a.ops, a.phases, coef);
+                    else if (rb == 3) batch_reg_forward<R, 3>(cur, P, a.ops, a.phases, coef);
+                    else batch_reg_forward<R, 2>(cur, P, a.ops, a.phases, coef);
                     for (uint32_t j = threadIdx.x; j < T; j += NT)
-                        psi[base | hioff[j >> P.nlow] | (j & lowmask)] = tp[swz_tile(j)];
+                        psi[base | hioff[j >> P.nlow] | (j & lowmask)] = cur[swz_tile(j)];
                     __syncthreads();
-                    continue;
                 }
+                continue;
+            }
+            for (uint64_t ti = 0; ti < ntl; ++ti) {
+                const uint64_t base = deposit(ti, P.out, P.nout);
                 for (uint32_t j = threadIdx.x; j < T; j += NT) tp[j] = psi[base | hioff[j >> P.nlow] | (j & lowmask)];
                 __syncthreads();
                 for (int o = P.op_begin; o < P.op_end; ++o) {
@@ -1773,9 +1783,17 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
             }
             __syncthreads();
             const ThreadCoset tc = thread_coset(C.kl);
-            for (uint64_t ci = 0; ci < (1ull << C.nfree); ++ci) {
+            const uint64_t ncos = 1ull << C.nfree;
+            const bool fast = (NT == 512) && (E == (uint32_t)EPT * 512u);
+            // cosets alternate between the two buffers (lambda's buffer is free
+            // here); the next one streams in while the current one is used
+            load_coset<R>(tp, psi, deposit(0, C.freeb, C.nfree), spanv, C.kl, E);
+            cp_async_commit();
+            for (uint64_t ci = 0; ci < ncos; ++ci) {
                 const uint64_t rep = deposit(ci, C.freeb, C.nfree);
-                for (uint32_t e = threadIdx.x; e < E; e += NT) tp[e] = psi[rep ^ spanv[e >> C.kl] ^ (e & lm)];
+                Cx<R> *cur = (ci & 1) ? tl : tp;
+                if (ci + 1 < ncos) load_coset<R>((ci & 1) ? tp : tl, psi, deposit(ci + 1, C.freeb, C.nfree), spanv, C.kl, E);
+                cp_async_commit();
                 Cx<R> acc[EPT];
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
@@ -1783,6 +1801,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                     acc[j] = mk<R>(0, 0);
                     if (hp > 0 && e < E) acc[j] = lam[rep ^ spanv[e >> C.kl] ^ (e & lm)];
                 }
+                cp_async_wait1();
                 __syncthreads();
                 for (int gi = C.g_begin; gi < C.g_end; ++gi) {
                     const DevGroup G = a.groups[gi];
@@ -1791,8 +1810,15 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                         const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
                         const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                         const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
-                        if (S.nY & 1) hpsi_one<R, EPT, true>(acc, tp, G.X, base, jm, g, E);
-                        else hpsi_one<R, EPT, false>(acc, tp, G.X, base, jm, g, E);
+                        if (fast) {
+                            const uint32_t sm = base ? ~jm : jm;
+                            if (S.nY & 1) hpsi_fast<R, EPT, true>(acc, cur, G.X, sm, g);
+                            else hpsi_fast<R, EPT, false>(acc, cur, G.X, sm, g);
+                        } else if (S.nY & 1) {
+                            hpsi_one<R, EPT, true>(acc, cur, G.X, base, jm, g, E);
+                        } else {
+                            hpsi_one<R, EPT, false>(acc, cur, G.X, base, jm, g, E);
+                        }
                     }
                 }
 #pragma unroll
@@ -1800,7 +1826,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                     const uint32_t e = threadIdx.x + j * NT;
                     if (e >= E) continue;
                     lam[rep ^ spanv[e >> C.kl] ^ (e & lm)] = acc[j];
-                    if (hp == a.nhpass - 1) eacc += (double)(tp[e].x * acc[j].x + tp[e].y * acc[j].y);
+                    if (hp == a.nhpass - 1) eacc += (double)(cur[e].x * acc[j].x + cur[e].y * acc[j].y);
                 }
                 __syncthreads();
             }
@@ -1882,6 +1908,53 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
         }
         __syncthreads();
     }
+}
+
+// ------------------------------------------------------------- Alg. 6 search --
+// One greedy step of Alg. 6 on the device: every global set G (an nG-subset
+// of the n qubits, by lexicographic rank r) counts the remaining strings
+// whose X/Y support avoids G (weights = multiplicities); the step takes the
+// largest count, ties to the smallest rank -- the first maximum in
+// lexicographic order, as the host search does.  best = max over
+// (count << 32) | (0xFFFFFFFF - r).
+__global__ void k_alg6_step(const uint64_t *__restrict__ xs, const int32_t *__restrict__ w, int nx, int n, int k,
+                            const int64_t *__restrict__ binom, uint64_t ncand, unsigned long long *best) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sx = reinterpret_cast<uint64_t *>(smem);
+    int32_t *sw = reinterpret_cast<int32_t *>(sx + nx);
+    int64_t *sb = reinterpret_cast<int64_t *>(sw + nx + (nx & 1));   // [(n + 1) * (k + 1)]: C(a, b)
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        sx[i] = xs[i];
+        sw[i] = w[i];
+    }
+    for (int i = threadIdx.x; i < (n + 1) * (k + 1); i += blockDim.x) sb[i] = binom[i];
+    __syncthreads();
+    unsigned long long mine = 0;
+    for (uint64_t r0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r0 < ncand; r0 += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t G = 0;
+        int64_t r = (int64_t)r0;
+        int c = 0;
+        for (int i = 0; i < k; ++i) {
+            while (true) {
+                const int a = n - c - 1, b = k - i - 1;
+                const int64_t cnt = (a >= 0 && b <= a) ? sb[a * (k + 1) + b] : 0;
+                if (r < cnt) break;
+                r -= cnt;
+                ++c;
+            }
+            G |= 1ull << c;
+            ++c;
+        }
+        unsigned int cnt = 0;
+        for (int i = 0; i < nx; ++i) cnt += (sx[i] & G) ? 0u : (unsigned int)sw[i];
+        const unsigned long long key = ((unsigned long long)cnt << 32) | (0xFFFFFFFFull - r0);
+        mine = key > mine ? key : mine;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, mine, o);
+        mine = other > mine ? other : mine;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(best, mine);
 }
 
 // ------------------------------------------------------------ small kernels --
@@ -2367,6 +2440,17 @@ cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, co
     else { SV_BATCH_SWITCH(double, ept, SV_BLAUNCH) }
 #undef SV_BLAUNCH
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alg6_step(cudaStream_t st, const uint64_t *xs, const int32_t *w, int nx, int n, int k,
+                             const int64_t *binom, uint64_t ncand, unsigned long long *best) {
+    const size_t sm = (size_t)nx * 8 + (size_t)(nx + (nx & 1)) * 4 + (size_t)(n + 1) * (k + 1) * 8;
+    const int threads = 256;
+    const uint64_t blocks = std::min<uint64_t>((ncand + threads - 1) / threads, (uint64_t)device_sms() * 8);
+    cudaError_t e = cudaFuncSetAttribute(k_alg6_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_alg6_step<<<(int)std::max<uint64_t>(blocks, 1), threads, sm, st>>>(xs, w, nx, n, k, binom, ncand, best);
     return cudaGetLastError();
 }
 

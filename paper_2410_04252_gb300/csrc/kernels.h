@@ -112,6 +112,10 @@ cudaError_t launch_energy(cudaStream_t st, const double *slotval, const int32_t 
 cudaError_t launch_copy(sv_dtype dt, cudaStream_t st, void *dst, const void *src, size_t n_elems);
 // One persistent launch over all states (512 threads per CTA).
 cudaError_t launch_batch(sv_dtype dt, cudaStream_t st, int grid, int threads, const BatchArgs &a);
+// One greedy step of Alg. 6 over the global sets of ranks [0, ncand): best receives
+// max over (count << 32) | (0xFFFFFFFF - rank); binom is C(a, b) as [(n + 1)][(k + 1)].
+cudaError_t launch_alg6_step(cudaStream_t st, const uint64_t *xs, const int32_t *w, int nx, int n, int k,
+                             const int64_t *binom, uint64_t ncand, unsigned long long *best);
 size_t batch_smem(sv_dtype dt, int kmax, int hio, int threads);
 // 0 when (dt, kmax, threads) has no instantiated kernel
 int batch_supported(sv_dtype dt, int kmax, int threads);

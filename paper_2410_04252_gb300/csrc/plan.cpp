@@ -743,7 +743,7 @@ void for_each_subset_rank(const std::vector<int> &fr, int k, int n, const Binom 
 // Counts are maintained incrementally: a support x adds its multiplicity to
 // every global set disjoint from it.
 std::string tiling_pauli_strings(int n, int nG, const sv_pauli *p, const std::vector<int32_t> &terms,
-                                 std::vector<std::vector<int32_t>> &tiles_terms,
+                                 const PlanOptions &o, std::vector<std::vector<int32_t>> &tiles_terms,
                                  std::vector<uint64_t> &tiles_local) {
     const uint64_t Q = bit(n) - 1;
     std::unordered_map<uint64_t, int32_t> xi;
@@ -763,7 +763,46 @@ std::string tiling_pauli_strings(int n, int nG, const sv_pauli *p, const std::ve
     }
     Binom B(n);
     int64_t ncand = B(n, nG);
-    if (ncand > 60000000) return "Alg. 6 search space C(n, n_G) too large";
+    auto unrank = [&](int64_t r) {
+        uint64_t G = 0;
+        int c = 0;
+        for (int i = 0; i < nG; ++i) {
+            while (true) {
+                int64_t cnt = B(n - c - 1, nG - i - 1);
+                if (r < cnt) break;
+                r -= cnt;
+                ++c;
+            }
+            G |= bit(c);
+            ++c;
+        }
+        return G;
+    };
+    if (o.alg6_step) {
+        // greedy steps on the device: counts recomputed per step, no table
+        std::vector<int32_t> w(xs.size());
+        for (size_t gi = 0; gi < xs.size(); ++gi) w[gi] = (int32_t)members[gi].size();
+        size_t left = xs.size();
+        while (left) {
+            int64_t bestr = -1, best = 0;
+            std::string e = o.alg6_step(xs, w, n, nG, bestr, best);
+            if (!e.empty()) return e;
+            if (best <= 0 || bestr < 0 || bestr >= ncand) return "no mapping holds a remaining Pauli string";
+            const uint64_t G = unrank(bestr);
+            std::vector<int32_t> tile;
+            for (size_t gi = 0; gi < xs.size(); ++gi) {
+                if (!w[gi] || (xs[gi] & G)) continue;
+                w[gi] = 0;
+                --left;
+                tile.insert(tile.end(), members[gi].begin(), members[gi].end());
+            }
+            std::sort(tile.begin(), tile.end());
+            tiles_terms.push_back(tile);
+            tiles_local.push_back(Q & ~G);
+        }
+        return "";
+    }
+    if (ncand > 60000000) return "Alg. 6 search space C(n, n_G) too large for the host search";
     std::vector<int64_t> count((size_t)ncand, 0);
     auto add = [&](size_t gi, int64_t w) {
         std::vector<int> fr;
@@ -778,22 +817,7 @@ std::string tiling_pauli_strings(int n, int nG, const sv_pauli *p, const std::ve
         for (int64_t r = 0; r < ncand; ++r)
             if (best < count[(size_t)r]) { best = count[(size_t)r]; bestr = r; }
         if (bestr < 0) return "no mapping holds a remaining Pauli string";
-        // unrank bestr -> global set
-        uint64_t G = 0;
-        {
-            int64_t r = bestr;
-            int c = 0;
-            for (int i = 0; i < nG; ++i) {
-                while (true) {
-                    int64_t cnt = B(n - c - 1, nG - i - 1);
-                    if (r < cnt) break;
-                    r -= cnt;
-                    ++c;
-                }
-                G |= bit(c);
-                ++c;
-            }
-        }
+        const uint64_t G = unrank(bestr);
         std::vector<int32_t> tile;
         for (size_t gi = 0; gi < xs.size(); ++gi) {
             if (!alive[gi] || (xs[gi] & G)) continue;
@@ -897,7 +921,7 @@ std::string plan_evc(int n, int g, const sv_pauli *p, const double *coeffs, size
     std::vector<std::vector<int32_t>> tt;
     std::vector<uint64_t> tl;
     if (lazy) {
-        std::string err = tiling_pauli_strings(n, g, p, narrow, tt, tl);
+        std::string err = tiling_pauli_strings(n, g, p, narrow, o, tt, tl);
         if (!err.empty()) return err;
         for (size_t i = 0; i < tt.size(); ++i) {
             Tile t;

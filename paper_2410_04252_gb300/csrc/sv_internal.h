@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -146,6 +147,13 @@ struct PlanOptions {
     int fuse_max = 0;            // gate operations per gate pass (0 = as many as fit)
     int hier_intra = -1;         // >= 0: hierarchical tiling (Alg. 4/5) with this many intra qubits
     int max_diag = kMaxPassDiag; // diagonal blocks per register-blocked pass (shared-memory budget)
+    // One greedy step of Alg. 6 done elsewhere (on the device): given the
+    // distinct X/Y supports xs with remaining weights w, return the rank of
+    // the first global set (lexicographic order) of maximal count and that
+    // count.  Empty: the host search with incrementally maintained counts.
+    std::function<std::string(const std::vector<uint64_t> &xs, const std::vector<int32_t> &w, int n, int nG,
+                              int64_t &rank, int64_t &count)>
+        alg6_step;
 };
 
 // Returns an empty string on success, else the error message.

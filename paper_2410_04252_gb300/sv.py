@@ -48,7 +48,7 @@ class Options(ctypes.Structure):
                 ("evc_low_bits", ctypes.c_int32), ("evc_span", ctypes.c_int32),
                 ("pad_highest", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("wait_limit", ctypes.c_int64), ("profile", ctypes.c_int32), ("fuse_max", ctypes.c_int32), ("intra_bits", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("wait_limit", ctypes.c_int64), ("profile", ctypes.c_int32), ("fuse_max", ctypes.c_int32), ("intra_bits", ctypes.c_int32), ("plan_device", ctypes.c_int32)]
 
 
 K_GATE, K_QR, K_EVC, K_HPSI, K_ADJ, K_PERM, K_AUX, K_BATCH = range(8)

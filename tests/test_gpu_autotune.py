@@ -115,3 +115,21 @@ def test_batch_rejects_unbuilt_shape():
     o.tile_bits, o.threads = 13, 256          # 32 amplitudes per thread: not built
     with pytest.raises(sv.SvError):
         sv.batch_run(n, sv.C64, circs, params, ham, options=o)
+
+
+@pytest.mark.parametrize("n,g,nterms,kind", [(10, 3, 40, "random"), (14, 4, 64, "jw"), (20, 5, 160, "random"),
+                                            (32, 6, 1024, "random"), (30, 6, 4096, "jw")])
+def test_alg6_search_on_device_matches_host(n, g, nterms, kind):
+    """The device search of Alg. 6 (one greedy step per launch, first maximum
+    in lexicographic order) gives the host search's plan bit for bit."""
+    h = W.random_hamiltonian(n, nterms, 5 + n) if kind == "random" else W.jw_hamiltonian(n, nterms, 5 + n)
+    x, z = W.pauli_masks(h)
+    od = sv.default_options(sv.C64)
+    od.plan_device = 1
+    oh = sv.default_options(sv.C64)
+    oh.plan_device = 2
+    pd = sv.plan_evc(n, g, x, z, sv.LAZY, od)
+    ph = sv.plan_evc(n, g, x, z, sv.LAZY, oh)
+    assert pd["order"] == ph["order"]
+    assert [(t["begin"], t["end"], t["local_mask"], t["pairs"]) for t in pd["tiles"]] == \
+        [(t["begin"], t["end"], t["local_mask"], t["pairs"]) for t in ph["tiles"]]
