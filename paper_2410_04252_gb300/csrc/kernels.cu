@@ -57,6 +57,32 @@ __device__ __forceinline__ void rot(Cx<R> &u, Cx<R> &v, R c, R s) {
     v = mk<R>(s * a.x + c * b.x, s * a.y + c * b.y);
 }
 
+// complex64: the same rotation on packed pairs (one f32x2 instruction per
+// real and imaginary part together; same rounding: one rounded product, then
+// a fused multiply-add)
+__device__ __forceinline__ unsigned long long f2_pack(float x, float y) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+template <>
+__device__ __forceinline__ void rot<float>(float2 &u, float2 &v, float c, float s) {
+    const unsigned long long U = f2_pack(u.x, u.y), V = f2_pack(v.x, v.y);
+    const unsigned long long C = f2_pack(c, c), S = f2_pack(s, s), NS = f2_pack(-s, -s);
+    unsigned long long t, uu, vv;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(V), "l"(NS));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(U), "l"(C), "l"(t));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(V), "l"(C));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(U), "l"(S), "l"(t));
+    u = f2_unpack(uu);
+    v = f2_unpack(vv);
+}
+
 template <typename R>
 __device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
     return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
