@@ -1557,6 +1557,34 @@ __device__ __forceinline__ void hpsi_fast(Cx<R> *acc, const Cx<R> *t, uint32_t X
     }
 }
 
+// complex64, 16 amplitudes per thread (NT = 512, E = 8192): the signed
+// coefficient of element j is built along a Gray chain written out (each
+// one XOR from an earlier one), and the partner of element j is at byte
+// offset B ^ (j << 12) of the staged coset (B = (t ^ X) * 8).
+template <bool ODD>
+__device__ __forceinline__ void hpsi_gray16(float2 *acc, const unsigned char *tb, uint32_t B, uint32_t g0,
+                                            uint32_t w) {
+    const uint32_t F0 = (w & 1u) << 31, F1 = (w & 2u) << 30, F2 = (w & 4u) << 29, F3 = (w & 8u) << 28;
+    const uint32_t g1 = g0 ^ F0, g2 = g0 ^ F1, g3 = g2 ^ F0, g4 = g0 ^ F2, g5 = g4 ^ F0, g6 = g4 ^ F1,
+                   g7 = g6 ^ F0, g8 = g0 ^ F3, g9 = g8 ^ F0, g10 = g8 ^ F1, g11 = g10 ^ F0, g12 = g8 ^ F2,
+                   g13 = g12 ^ F0, g14 = g12 ^ F1, g15 = g14 ^ F0;
+#define SV_HG(J)                                                                                 \
+    {                                                                                            \
+        const float2 v = *reinterpret_cast<const float2 *>(tb + (B ^ ((uint32_t)(J) << 12)));   \
+        const float f = __uint_as_float(g##J);                                                   \
+        if (ODD) {                                                                               \
+            acc[J].x -= f * v.y;                                                                 \
+            acc[J].y += f * v.x;                                                                 \
+        } else {                                                                                 \
+            acc[J].x += f * v.x;                                                                 \
+            acc[J].y += f * v.y;                                                                 \
+        }                                                                                        \
+    }
+    SV_HG(0) SV_HG(1) SV_HG(2) SV_HG(3) SV_HG(4) SV_HG(5) SV_HG(6) SV_HG(7)
+    SV_HG(8) SV_HG(9) SV_HG(10) SV_HG(11) SV_HG(12) SV_HG(13) SV_HG(14) SV_HG(15)
+#undef SV_HG
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
                                                       const CosetArgs a, const DevGroup *__restrict__ groups,
@@ -1598,8 +1626,18 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
             for (int s = G.s_begin; s < G.s_end; ++s) {
                 const DevString S = strs[s];
                 const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
-                const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                 const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
+                if constexpr (sizeof(R) == 4 && EPT == 16) {
+                    if (fast) {
+                        const uint32_t g0 = __float_as_uint((float)g) ^ ((uint32_t)base << 31);
+                        const uint32_t B = (threadIdx.x ^ G.X) * 8u;
+                        const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(t);
+                        if (S.nY & 1) hpsi_gray16<true>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                        else hpsi_gray16<false>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                        continue;
+                    }
+                }
+                const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                 if (fast) {
                     const uint32_t sm = base ? ~jm : jm;
                     if (S.nY & 1) hpsi_fast<R, EPT, true>(acc, t, G.X, sm, g);
@@ -1834,8 +1872,20 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                     for (int s = G.s_begin; s < G.s_end; ++s) {
                         const DevString S = a.strs[s];
                         const int base = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1;
-                        const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                         const R g = (S.nY & 2) ? -(R)S.coef : (R)S.coef;
+                        if constexpr (sizeof(R) == 4 && EPT == 16) {
+                            if (fast) {
+                                const uint32_t g0 = __float_as_uint((float)g) ^ ((uint32_t)base << 31);
+                                const uint32_t B = (threadIdx.x ^ G.X) * 8u;
+                                const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(cur);
+                                if (S.nY & 1)
+                                    hpsi_gray16<true>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                                else
+                                    hpsi_gray16<false>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                                continue;
+                            }
+                        }
+                        const uint32_t jm = walsh_mask(S.bz >> tc.ash);
                         if (fast) {
                             const uint32_t sm = base ? ~jm : jm;
                             if (S.nY & 1) hpsi_fast<R, EPT, true>(acc, cur, G.X, sm, g);
