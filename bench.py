@@ -396,6 +396,21 @@ def run_ours(args):
         ho.intra_bits = 0
         sim.set_options(ho)
 
+    # diagonal gates exempt from locality (not the paper's method)
+    ldiag = None
+    if not args.no_direct:
+        step(sv.LAZY_DIAG)
+        torch.cuda.synchronize()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        xe, xg = step(sv.LAZY_DIAG)
+        xst = sim.last_stats
+        x1.record(stream)
+        x1.synchronize()
+        ldiag = {"ms_per_step": x0.elapsed_time(x1), "qsu_qrs": xst.qsu_qrs, "evc_qrs": xst.evc_qrs,
+                 "energy_diff_vs_lazy": abs(xe - e)}
+
     if rank != 0:
         if dist is not None:
             dist.barrier()
@@ -450,6 +465,7 @@ def run_ours(args):
         "eager": eager,
         "direct": direct,
         "hier": hier,
+        "lazy_diag": ldiag,
         "energy": e,
         "plan_and_warmup_s": plan_s,
     }
@@ -567,6 +583,16 @@ def plan_table(args):
                                                 if inter[i] != inter[i - 1] and p["tiles"][i]["pairs"])
             row["adhoc_over_flat"] = row["adhoc_qrs"] / max(row["flat_qrs"], 1)
             rows.append(row)
+    # diagonal exemption (RZ / CZ never ask for a QR) vs the paper's lazy plan,
+    # random RY / RZ / CZ circuits of 20n gates
+    drows = []
+    for n in range(20, 37, 4):
+        c = W.random_circuit(n, 20 * n, 4000 + n, (W.RY, W.RZ, W.CZ))
+        row = {"n": n, "ops": c.m}
+        for name, sched in (("lazy", sv.LAZY), ("lazy_diag", sv.LAZY_DIAG), ("adhoc", sv.EAGER)):
+            p = sv.plan_qsu(n, g, c, sched)
+            row[name + "_qrs"] = sum(1 for t in p["tiles"] if t["pairs"])
+        drows.append(row)
     # EVC (Sec. V-B-2): Alg. 6 with diagonalization vs the index-order ad hoc
     # rule, JW-shaped Hamiltonians of 4096 strings on 32 chunks
     erows = []
@@ -584,7 +610,9 @@ def plan_table(args):
     print(json.dumps({"table": "QSU QR counts, flat vs hierarchical vs ad hoc (plan level)", "g": g,
                       "n_intra": nintra, "layers": "4n", "rows": rows,
                       "evc_table": "EVC QR counts, Alg. 6 lazy vs index-order ad hoc, JW-shaped 4096 strings",
-                      "evc_rows": erows}), flush=True)
+                      "evc_rows": erows,
+                      "diag_table": "QSU QR counts with diagonal gates exempt, random RY/RZ/CZ circuits",
+                      "diag_rows": drows}), flush=True)
     return 0
 
 

@@ -52,7 +52,14 @@ typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
  * plan has one tile and no QR -- gate passes and coset passes may pair
  * amplitudes of different chunks.  It is the single-GPU optimum the two
  * schedules are compared against. */
-typedef enum { SV_SCHED_EAGER = 0, SV_SCHED_LAZY = 1, SV_SCHED_DIRECT = 2, SV_SCHED_HIER = 3 } sv_schedule;
+typedef enum {
+    SV_SCHED_EAGER = 0, SV_SCHED_LAZY = 1, SV_SCHED_DIRECT = 2, SV_SCHED_HIER = 3, SV_SCHED_LAZY_DIAG = 4
+} sv_schedule;
+/* SV_SCHED_LAZY_DIAG: LAZY with diagonal gates (RZ, CZ) exempt from
+ * locality, as the paper's diagonalization exempts Z letters in EVC: a
+ * diagonal gate on global qubits is a phase per chunk (per staged tile), so
+ * it never asks for a QR; tiles grow past it and Alg. 3 ignores it.  Not the
+ * paper's QSU method: compared against it.  EVC under it is the LAZY one. */
 /* SV_SCHED_HIER: QSU by hierarchical tiling (Alg. 4 with Alg. 5) for a
  * two-layered interconnect whose intra-node part holds options.intra_bits of
  * the g global qubits (Q_intra starts at physical positions n-g ..

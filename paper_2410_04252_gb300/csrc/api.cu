@@ -360,7 +360,8 @@ bool alg6_on_device(int plan_device, int n, int g) {
 }
 
 sv_status check_sched(sv_schedule s) {
-    if (s != SV_SCHED_EAGER && s != SV_SCHED_LAZY && s != SV_SCHED_DIRECT && s != SV_SCHED_HIER)
+    if (s != SV_SCHED_EAGER && s != SV_SCHED_LAZY && s != SV_SCHED_DIRECT && s != SV_SCHED_HIER &&
+        s != SV_SCHED_LAZY_DIAG)
         return fail(SV_EINVAL, "bad schedule");
     return SV_OK;
 }
@@ -381,6 +382,7 @@ sv_status get_qsu(sv_handle *h, const sv_gate *gates, size_t m, size_t np, sv_sc
     auto t0 = std::chrono::steady_clock::now();
     PlanOptions po = plan_options(h->opt);
     if (sched == SV_SCHED_HIER) po.hier_intra = h->opt.intra_bits;
+    po.diag_exempt = sched == SV_SCHED_LAZY_DIAG;
     po.max_diag = h->dt == SV_C64 ? kMaxPassDiag : 3;     // complex128 tables are twice as large
     std::string err = plan_qsu(h->n, sched == SV_SCHED_DIRECT ? 0 : h->g, gates, m, sched != SV_SCHED_EAGER, po,
                                h->l2p, ent->plan);
@@ -1094,6 +1096,7 @@ sv_status sv_plan_qsu(int n, int g, const sv_gate *gates, size_t m, sv_schedule 
     SV_TRY(check_sched(sched));
     PlanOptions po = plan_options(o);
     if (sched == SV_SCHED_HIER) po.hier_intra = o.intra_bits;
+    po.diag_exempt = sched == SV_SCHED_LAZY_DIAG;
     err = plan_qsu(n, sched == SV_SCHED_DIRECT ? 0 : g, gates, m, sched != SV_SCHED_EAGER, po, l2p, p->q);
     if (!err.empty()) {
         delete p;

@@ -181,6 +181,37 @@ __device__ __noinline__ void apply_dense_op(Cx<R> *t, int k, const DevOp op, con
 // Apply one narrow gate to a staged tile of 2^k amplitudes (tile-local bit
 // positions in op.t).  U = exp(-i theta G/2); adj applies U^dagger.
 // Each thread owns whole index groups, so the caller syncs between gates.
+// Diagonal gates on qubits outside the staged tile (diagonal exemption)
+// become, for one tile, one of these operations: a phase on the whole tile
+// (RZ; t[0] = the qubit's bit in this tile), Z on an in-tile bit t[0] (CZ
+// whose outside qubit is 1 here), -1 on the whole tile (CZ of two outside
+// qubits that are both 1), or nothing.
+enum { SV_OP_PHASE = 100, SV_OP_ZSIGN = 101, SV_OP_NEG = 102, SV_OP_NOP = 103 };
+
+__device__ __forceinline__ DevOp resolve_out(DevOp op, uint64_t gbase) {
+    if (op.kind == SV_RZ && op.t[0] >= kOutTarget) {
+        op.t[0] = (int8_t)((gbase >> (op.t[0] - kOutTarget)) & 1ull);
+        op.kind = SV_OP_PHASE;
+    } else if (op.kind == SV_CZ && (op.t[0] >= kOutTarget || op.t[1] >= kOutTarget)) {
+        const bool o0 = op.t[0] >= kOutTarget, o1 = op.t[1] >= kOutTarget;
+        const int b0 = o0 ? (int)((gbase >> (op.t[0] - kOutTarget)) & 1ull) : 0;
+        const int b1 = o1 ? (int)((gbase >> (op.t[1] - kOutTarget)) & 1ull) : 0;
+        if (o0 && o1) {
+            op.kind = (b0 & b1) ? SV_OP_NEG : SV_OP_NOP;
+        } else if (o0 ? b0 : b1) {
+            op.t[0] = o0 ? op.t[1] : op.t[0];
+            op.kind = SV_OP_ZSIGN;
+        } else {
+            op.kind = SV_OP_NOP;
+        }
+    }
+    return op;
+}
+
+__device__ __forceinline__ bool has_out_target(const DevOp &op) {
+    return op.t[0] >= kOutTarget || (op.kind == SV_CZ && op.t[1] >= kOutTarget);
+}
+
 template <typename R>
 __device__ void apply_op(Cx<R> *t, int k, const DevOp &op, const R *coef, const Cx<R> *mats, bool adj) {
     const uint32_t T = 1u << k;
@@ -219,6 +250,29 @@ __device__ void apply_op(Cx<R> *t, int k, const DevOp &op, const R *coef, const 
             const Cx<R> v = t[i];
             t[i] = mk<R>(-v.x, -v.y);
         }
+        break;
+    }
+    case SV_OP_PHASE: {
+        const R c = coef[2 * op.gate];
+        const R s = adj ? -coef[2 * op.gate + 1] : coef[2 * op.gate + 1];
+        const R ss = op.t[0] ? s : -s;
+        for (uint32_t p = tid; p < T; p += nt) {
+            const Cx<R> v = t[p];
+            t[p] = mk<R>(c * v.x - ss * v.y, c * v.y + ss * v.x);
+        }
+        break;
+    }
+    case SV_OP_ZSIGN: {
+        const int b = op.t[0];
+        for (uint32_t p = tid; p < T / 2; p += nt) {
+            const uint32_t i = ins0(p, b) | (1u << b);
+            const Cx<R> v = t[i];
+            t[i] = mk<R>(-v.x, -v.y);
+        }
+        break;
+    }
+    case SV_OP_NEG: {
+        for (uint32_t p = tid; p < T; p += nt) t[p] = mk<R>(-t[p].x, -t[p].y);
         break;
     }
     case SV_GIVENS: {
@@ -309,6 +363,26 @@ __device__ R adjoint_op(Cx<R> *tp, Cx<R> *tl, int k, const DevOp &op, const R *c
         }
         break;
     }
+    case SV_OP_PHASE: {
+        // RZ on a qubit outside the tile: its bit is the same for every amplitude here
+        const R c = coef[2 * op.gate], s = -coef[2 * op.gate + 1];
+        const bool one = op.t[0] != 0;
+        const R ss = one ? s : -s;
+        for (uint32_t p = tid; p < T; p += nt) {
+            Cx<R> pv = tp[p], lv = tl[p];
+            const R im = lv.x * pv.y - lv.y * pv.x;
+            g += one ? -im : im;
+            tp[p] = mk<R>(c * pv.x - ss * pv.y, c * pv.y + ss * pv.x);
+            tl[p] = mk<R>(c * lv.x - ss * lv.y, c * lv.y + ss * lv.x);
+        }
+        break;
+    }
+    case SV_OP_ZSIGN:
+    case SV_OP_NEG:
+    case SV_OP_NOP:
+        apply_op<R>(tp, k, op, coef, mats, true);
+        apply_op<R>(tl, k, op, coef, mats, true);
+        break;
     case SV_GIVENS: {
         const R c = coef[2 * op.gate], s = -coef[2 * op.gate + 1];
         const int qa = op.t[0], qb = op.t[1];
@@ -351,7 +425,7 @@ __device__ R adjoint_op(Cx<R> *tp, Cx<R> *tl, int k, const DevOp &op, const R *c
 }
 
 __device__ __forceinline__ bool has_param(int kind) {
-    return kind == SV_RY || kind == SV_RZ || kind == SV_GIVENS || kind == SV_DEXC;
+    return kind == SV_RY || kind == SV_RZ || kind == SV_GIVENS || kind == SV_DEXC || kind == SV_OP_PHASE;
 }
 
 // ------------------------------------------------------------------ K-GATE --
@@ -374,7 +448,7 @@ __global__ void __launch_bounds__(512) k_gate_pass(Cx<R> *__restrict__ psi, cons
             tile[j] = psi[base | hioff[j >> a.nlow] | (j & lowmask)];
         __syncthreads();
         for (int o = a.op_begin; o < a.op_end; ++o) {
-            const DevOp op = ops[o];
+            const DevOp op = resolve_out(ops[o], base);
             apply_op<R>(tile, a.k, op, coef, mats, false);
             __syncthreads();
         }
@@ -413,7 +487,7 @@ __global__ void __launch_bounds__(512) k_adj_pass(Cx<R> *__restrict__ psi, Cx<R>
         }
         __syncthreads();
         for (int o = a.op_end - 1; o >= a.op_begin; --o) {
-            const DevOp op = ops[o];
+            const DevOp op = resolve_out(ops[o], base);
             R g = adjoint_op<R>(tp, tl, a.k, op, coef, mats);
             if (has_param(op.kind)) {
                 g = warp_sum<R>(g);
@@ -572,6 +646,29 @@ __device__ __forceinline__ void reg_apply(Cx<R> *x, const DevOp &op, uint32_t rm
         }
         break;
     }
+    case SV_OP_PHASE: {
+        const R c = coef[2 * op.gate], s = adj ? -coef[2 * op.gate + 1] : coef[2 * op.gate + 1];
+        const R ss = op.t[0] ? s : -s;
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = mk<R>(c * x[v].x - ss * x[v].y, c * x[v].y + ss * x[v].x);
+        break;
+    }
+    case SV_OP_ZSIGN: {
+        if ((rmask >> t0) & 1u) {
+#define SV_C(B) reg_neg_bit<R, V, B>(x)
+            SV_REG_SWITCH(b0, SV_C)
+#undef SV_C
+        } else if ((base >> t0) & 1u) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = mk<R>(-x[v].x, -x[v].y);
+        }
+        break;
+    }
+    case SV_OP_NEG: {
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = mk<R>(-x[v].x, -x[v].y);
+        break;
+    }
     default:
         break;
     }
@@ -619,14 +716,15 @@ __device__ __forceinline__ R reg_adjoint(Cx<R> *p, Cx<R> *l, const DevOp &op, ui
 #define SV_C(B) g = reg_ry_adj<R, V, B>(p, l, c, s)
         SV_REG_SWITCH(b0, SV_C)
 #undef SV_C
-    } else if (op.kind == SV_RZ) {
+    } else if (op.kind == SV_RZ || op.kind == SV_OP_PHASE) {
         const R c = coef[2 * op.gate], s = -coef[2 * op.gate + 1];
-        if ((rmask >> t0) & 1u) {
+        if (op.kind == SV_RZ && ((rmask >> t0) & 1u)) {
 #define SV_C(B) g = reg_rz_adj<R, V, B>(p, l, c, s)
             SV_REG_SWITCH(b0, SV_C)
 #undef SV_C
         } else {
-            const bool one = (base >> t0) & 1u;
+            // the bit is the same for all registers: a thread bit, or a qubit outside the tile
+            const bool one = op.kind == SV_OP_PHASE ? op.t[0] != 0 : ((base >> t0) & 1u) != 0;
             const R ss = one ? s : -s;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
@@ -810,6 +908,7 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
             for (int o = P.op_begin; o < P.op_end;) {
                 const StagedOp<R> x_op = so[o - a.op_begin];
                 DevOp op = x_op.op;
+                if (has_out_target(op)) op = resolve_out(op, gbase);
                 if (op.mat <= -2) {                  // a diagonal block: all its members at once
                     const int bi = -2 - op.mat;
                     diag_apply<R, RB>(x, bi - a.db_begin, dR, dC, dM);
@@ -910,6 +1009,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
             for (int o = P.op_end - 1; o >= P.op_begin;) {
                 const StagedOp<R> x_op = so[o - a.op_begin];
                 DevOp op = x_op.op;
+                if (has_out_target(op)) op = resolve_out(op, gbase);
                 if (op.mat <= -2) {
                     // a diagonal block: every member's generator expectation
                     // at the block's end (Z commutes with the block), then

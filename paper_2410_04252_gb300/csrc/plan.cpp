@@ -129,9 +129,36 @@ void qr_pairs(std::vector<int32_t> &l2p, uint64_t old_loc, uint64_t new_loc, std
     }
 }
 
+bool is_diag_op(const Op &op) { return op.kind == SV_RZ || op.kind == SV_CZ; }
+
+// Alg. 2 with diagonal gates exempt from locality: a diagonal gate is taken
+// when no earlier skipped gate shares a qubit with it, whatever its targets.
+void tile_construction_dx(uint64_t QL, const std::vector<int32_t> &remain, const std::vector<Op> &ops,
+                          std::vector<int32_t> &G, uint64_t Q) {
+    uint64_t blocked = 0;
+    G.clear();
+    for (int32_t u : remain) {
+        const uint64_t t = ops[u].tmask;
+        const bool ok = (t & blocked) == 0 && (is_diag_op(ops[u]) || (t & ~QL) == 0);
+        if (ok) G.push_back(u);
+        else blocked |= t;
+        if ((blocked & Q) == Q) break;
+    }
+}
+
+// Alg. 3 with diagonal gates exempt: they neither claim local qubits nor block.
+uint64_t qubit_mapping_dx(uint64_t Q, const std::vector<int32_t> &remain, const std::vector<Op> &ops, int nL,
+                          bool pad_highest) {
+    std::vector<int32_t> nd;
+    for (int32_t u : remain)
+        if (!is_diag_op(ops[u])) nd.push_back(u);
+    if (nd.empty()) return 0;
+    return qubit_mapping(Q, nd, ops, nL, pad_highest);
+}
+
 std::string flat_tiling(int n, int nL, const std::vector<Op> &ops, bool pad_highest,
                         std::vector<int32_t> l2p, std::vector<int32_t> &order, std::vector<Tile> &tiles,
-                        std::vector<int32_t> &final_l2p) {
+                        std::vector<int32_t> &final_l2p, bool dx) {
     const uint64_t Q = (n == 64) ? ~0ull : (bit(n) - 1);
     uint64_t cur = local_set(l2p, nL);
     uint64_t QL = cur;
@@ -139,7 +166,8 @@ std::string flat_tiling(int n, int nL, const std::vector<Op> &ops, bool pad_high
     std::vector<char> taken(ops.size(), 0);
     int stall = 0;
     while (!remain.empty()) {
-        tile_construction(QL, remain, ops, G);
+        if (dx) tile_construction_dx(QL, remain, ops, G, Q);
+        else tile_construction(QL, remain, ops, G);
         if (!G.empty()) {
             Tile t;
             t.begin = (int32_t)order.size();
@@ -160,7 +188,7 @@ std::string flat_tiling(int n, int nL, const std::vector<Op> &ops, bool pad_high
             return "flat tiling made no progress";
         }
         if (remain.empty()) break;
-        QL = qubit_mapping(Q, remain, ops, nL, pad_highest);
+        QL = dx ? qubit_mapping_dx(Q, remain, ops, nL, pad_highest) : qubit_mapping(Q, remain, ops, nL, pad_highest);
         if (!QL) return "qubit mapping returned an empty set";
     }
     final_l2p = l2p;
@@ -278,7 +306,7 @@ std::string adhoc_schedule(int n, int nL, const std::vector<Op> &ops, const std:
 // the earliest remaining gates), padded with the lowest free local bits; the
 // pass then takes gates like Alg. 2 (a gate that does not fit blocks its
 // targets), which keeps the dependency order C1.
-void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, int fuse_max) {
+void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, int fuse_max, bool dx) {
     const int nL = P.nL;
     const int cap = (fuse_max > 0 && fuse_max < kMaxPassOps) ? fuse_max : kMaxPassOps;
     k = std::min(k, nL);
@@ -289,7 +317,8 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, in
         const Tile &T = P.tiles[ti];
         std::vector<int32_t> remain(P.order.begin() + T.begin, P.order.begin() + T.end);
         std::vector<uint64_t> pm(ops.size(), 0);
-        for (int32_t u : remain) pm[u] = to_physical(ops[u].tmask, T.l2p);
+        // under the diagonal exemption only the local targets of a gate are staged
+        for (int32_t u : remain) pm[u] = to_physical(ops[u].tmask, T.l2p) & (dx ? localbits : ~0ull);
         std::vector<int32_t> G, next;
         while (!remain.empty()) {
             uint64_t S = lowmask, avail = localbits;
@@ -324,8 +353,11 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, in
             for (int32_t u : G) {
                 DevOp d;
                 d.kind = ops[u].kind;
-                for (int i = 0; i < 4; ++i)
-                    d.t[i] = (int8_t)(i < ops[u].nq ? loc[T.l2p[ops[u].q[i]]] : -1);
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= ops[u].nq) { d.t[i] = -1; continue; }
+                    const int pb = T.l2p[ops[u].q[i]];
+                    d.t[i] = (int8_t)((S >> pb & 1) ? loc[pb] : kOutTarget + pb);
+                }
                 d.gate = u;
                 d.mat = ops[u].mat;
                 P.ops.push_back(d);
@@ -367,7 +399,8 @@ void plan_phases(QsuPlan &P) {
         auto tmask = [&](const DevOp &d) {
             uint32_t m = 0;
             const int nq = (d.kind == SV_CZ) ? 2 : 1;
-            for (int i = 0; i < nq; ++i) m |= 1u << d.t[i];
+            for (int i = 0; i < nq; ++i)
+                if (d.t[i] < kOutTarget) m |= 1u << d.t[i];
             return m;
         };
         std::vector<DevOp> remain(P.ops.begin() + gp.op_begin, P.ops.begin() + gp.op_end), next, out;
@@ -417,17 +450,23 @@ void plan_phases(QsuPlan &P) {
 // commute with each other), so that they gather into long runs; a
 // non-diagonal operation that shares a qubit with a delayed diagonal one
 // first flushes the delayed ones.  The order stays a valid schedule (C1).
+bool in_tile_diag(const DevOp &d) {
+    return diag_kind(d.kind) && d.t[0] < kOutTarget && (d.kind != SV_CZ || d.t[1] < kOutTarget);
+}
+
 void cluster_diagonals(QsuPlan &P, const Phase &F) {
     auto tm = [](const DevOp &d) {
-        uint32_t m = 1u << d.t[0];
-        if (d.kind == SV_CZ) m |= 1u << d.t[1];
+        uint32_t m = 0;
+        const int nq = d.kind == SV_CZ ? 2 : 1;
+        for (int i = 0; i < nq; ++i)
+            if (d.t[i] < kOutTarget) m |= 1u << d.t[i];
         return m;
     };
     std::vector<DevOp> out, pend;
     uint32_t pmask = 0;
     for (int o = F.op_begin; o < F.op_end; ++o) {
         const DevOp &d = P.ops[o];
-        if (diag_kind(d.kind)) {
+        if (in_tile_diag(d)) {
             pend.push_back(d);
             pmask |= tm(d);
             continue;
@@ -461,9 +500,9 @@ void plan_diag_blocks(QsuPlan &P, int max_diag) {
             cluster_diagonals(P, F);
             int o = F.op_begin;
             while (o < F.op_end) {
-                if (!diag_kind(P.ops[o].kind)) { ++o; continue; }
+                if (!in_tile_diag(P.ops[o])) { ++o; continue; }
                 int e = o;
-                while (e < F.op_end && diag_kind(P.ops[e].kind)) ++e;
+                while (e < F.op_end && in_tile_diag(P.ops[e])) ++e;
                 if (diag_run_pays(P, o, e) && (int)P.dblocks.size() - gp.db_begin < max_diag) {
                     DiagBlock B;
                     B.op_begin = o;
@@ -893,14 +932,14 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
         err = hierarchical_tiling(n, P.nL, o.hier_intra, ops, o.pad_highest, l2p_init, P.order, P.tiles,
                                   P.final_l2p);
     } else if (lazy) {
-        err = flat_tiling(n, P.nL, ops, o.pad_highest, l2p_init, P.order, P.tiles, P.final_l2p);
+        err = flat_tiling(n, P.nL, ops, o.pad_highest, l2p_init, P.order, P.tiles, P.final_l2p, o.diag_exempt);
     } else {
         err = adhoc_schedule(n, P.nL, ops, depth_sort(ops), l2p_init, P.order, P.tiles, P.final_l2p);
     }
     if (!err.empty()) return err;
     if (P.tiles.empty()) P.final_l2p = l2p_init;
     int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
-    plan_gate_passes(P, ops, k, o.low_bits, o.fuse_max);
+    plan_gate_passes(P, ops, k, o.low_bits, o.fuse_max, o.diag_exempt);
     plan_phases(P);
     plan_diag_blocks(P, std::min(o.max_diag, kMaxPassDiag));
     return "";

@@ -36,7 +36,11 @@ struct Tile {
     uint64_t intra_mask = 0;         // hierarchical tiling: logical intra set Q_intra (Alg. 4/5)
 };
 
-// Device-side gate of a pass: kind, targets as TILE-LOCAL bit positions.
+// Device-side gate of a pass: kind, targets as TILE-LOCAL bit positions.  A
+// target t >= kOutTarget is outside the staged tile (only diagonal gates on
+// global qubits under the diagonal exemption): physical bit t - kOutTarget,
+// constant over a tile.
+constexpr int kOutTarget = 64;
 struct DevOp {
     int32_t kind;
     int8_t t[4];
@@ -147,6 +151,7 @@ struct PlanOptions {
     int fuse_max = 0;            // gate operations per gate pass (0 = as many as fit)
     int hier_intra = -1;         // >= 0: hierarchical tiling (Alg. 4/5) with this many intra qubits
     int max_diag = kMaxPassDiag; // diagonal blocks per register-blocked pass (shared-memory budget)
+    bool diag_exempt = false;    // QSU: diagonal gates (RZ, CZ) never ask for a QR (per-chunk phases)
     // One greedy step of Alg. 6 done elsewhere (on the device): given the
     // distinct X/Y supports xs with remaining weights w, return the rank of
     // the first global set (lexicographic order) of maximal count and that

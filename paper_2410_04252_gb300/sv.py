@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 SV_OK, SV_EINVAL, SV_ENOMEM, SV_ECUDA, SV_EPLAN, SV_ETIMEOUT, SV_EDEVICE, SV_ESTATE = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EPLAN", "ETIMEOUT", "EDEVICE", "ESTATE"]
 C64, C128 = 0, 1
-EAGER, LAZY, DIRECT, HIER = 0, 1, 2, 3
+EAGER, LAZY, DIRECT, HIER, LAZY_DIAG = 0, 1, 2, 3, 4
 KEEP_LAYOUT, FORWARD_DONE = 1, 2
 
 

@@ -342,3 +342,26 @@ def test_register_passes_full_tiles(dtype, fuse_max):
     tol = 1e-4 * l1(h) if dtype == sv.C64 else 1e-10 * l1(h)
     assert abs(e - ograd.objective(c, p, h)) < tol
     assert np.max(np.abs(gr - ograd.parameter_shift(c, p, h))) < tol
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("n,g,kinds", [(14, 4, "rzcz"), (16, 3, "rzcz"), (13, 3, "givens")])
+def test_diagonal_exemption_schedule(dtype, n, g, kinds):
+    """LAZY_DIAG: diagonal gates on global qubits applied as per-tile phases /
+    signs (register-phased passes for RY/RZ/CZ circuits, plain passes when a
+    Givens gate is in the pass): state, energy and gradient = oracle."""
+    ks = (W.RY, W.RZ, W.CZ) if kinds == "rzcz" else (W.RY, W.RZ, W.CZ, W.GIVENS)
+    c = W.random_circuit(n, 160, 300 + n + g, ks)
+    p = W.uniform_params(c.nparams, 301 + n, -math.pi, math.pi)
+    s = sv.StateVector(n, g, dtype)
+    s.reset(5)
+    st = s.apply_circuit(c, p, sv.LAZY_DIAG)
+    lz = sv.plan_qsu(n, g, c, sv.LAZY)
+    assert st.qsu_qrs <= sum(1 for t in lz["tiles"] if t["pairs"])
+    ref = oracle_state(c, p, 5)
+    assert np.max(np.abs(s.get_state() - ref)) < AMP_TOL[dtype]
+    h = W.random_hamiltonian(n, 48, 302 + n)
+    e, gr, _ = s.vqe_step(5, c, p, h, sv.LAZY_DIAG)
+    tol = 1e-4 * l1(h) if dtype == sv.C64 else 1e-7
+    assert abs(e - ograd.objective(c, p, h, 5)) < tol
+    assert np.max(np.abs(gr - ograd.finite_difference(c, p, h, 5))) < tol

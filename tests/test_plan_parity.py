@@ -251,3 +251,27 @@ def test_qsu_experiment_qr_trends():
     assert all(b > a for a, b in zip(adhoc, adhoc[1:]))
     ratio = adhoc[3] / flat[3]
     assert 71 / 2 < ratio < 71 * 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_diagonal_exemption_plan(seed):
+    """LAZY_DIAG: every gate once, C1 order, non-diagonal gates narrow under
+    their tile's mapping (diagonal ones may touch global qubits), and no more
+    QRs than the paper's lazy plan on these circuits."""
+    n, g = 14 + seed % 5, 3 + seed % 3
+    c = W.random_circuit(n, 200, 900 + seed, (W.RY, W.RZ, W.CZ, W.GIVENS))
+    dx = sv.plan_qsu(n, g, c, sv.LAZY_DIAG)
+    lz = sv.plan_qsu(n, g, c, sv.LAZY)
+    assert sorted(dx["order"]) == list(range(c.m))
+    pos = {u: i for i, u in enumerate(dx["order"])}
+    for a_ in range(c.m):
+        for b_ in range(a_ + 1, c.m):
+            if set(c.targets(a_)) & set(c.targets(b_)):
+                assert pos[a_] < pos[b_]
+    for t in dx["tiles"]:
+        for u in dx["order"][t["begin"]:t["end"]]:
+            if int(c.kinds[u]) in (W.RZ, W.CZ):
+                continue
+            assert all(t["local_mask"] >> q & 1 for q in c.targets(u))
+    nq = lambda p: sum(1 for t in p["tiles"] if t["pairs"])
+    assert nq(dx) <= nq(lz)
