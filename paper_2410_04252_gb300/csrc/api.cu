@@ -111,7 +111,7 @@ CosetArgs coset_args(int n, const CosetPass &cp) {
     a.g_end = cp.g_end;
     a.s_begin = cp.s_begin;
     a.s_end = cp.s_end;
-    a.few = (cp.g_end - cp.g_begin) <= 8 && (cp.s_end - cp.s_begin) == (cp.g_end - cp.g_begin);
+    a.few = (cp.g_end - cp.g_begin) <= kEvcFew && (cp.s_end - cp.s_begin) == (cp.g_end - cp.g_begin);
     return a;
 }
 

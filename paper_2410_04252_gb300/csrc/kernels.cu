@@ -1477,7 +1477,6 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
 // are computed once per kernel; per coset each group adds its FP32 partial
 // into a per-thread shared-memory slot (the state's real type), flushed into
 // FP64 registers every 64 cosets; one FP64 reduction at the end.
-constexpr int kEvcFew = 8;
 
 template <typename R, int EPT, bool ODD>
 __device__ __forceinline__ R evc_pairs(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sel, int base,

@@ -42,6 +42,9 @@ struct DevString {
     uint32_t bz;      // parities of the pass's span basis against z
 };
 
+// Few-string expectation passes (every group one string): at most this many groups.
+constexpr int kEvcFew = 8;
+
 // Batched kernel arguments (see K-BATCH in kernels.cu).
 struct BatchArgs {
     int n, nstates, nhpass;
