@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
     }
 }
 
-template <typename R, int RB, bool PREF>
+template <typename R, int RB>
 __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
                                                     const GatePassArgs a, const DevOp *__restrict__ ops,
                                                     const Phase *__restrict__ phases, const R *__restrict__ coef,
@@ -945,12 +945,11 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const uint32_t nh = 1u << (a.k - a.nlow);
     const int nops = a.op_end - a.op_begin;
     const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // shared memory: lambda tile, then psi tiles (two when PREF: the next
-    // tile's psi streams in while the current one is processed)
+    // shared memory: lambda tile, then the psi tile
     const int nb = a.db_end - a.db_begin;
     Cx<R> *tl = reinterpret_cast<Cx<R> *>(smem);
-    Cx<R> *tps = tl + T;
-    Cx<R> *dC = tps + (PREF ? 2 : 1) * T;                     // [nb][NT] diagonal-block thread factors (of D^dagger)
+    Cx<R> *tp = tl + T;
+    Cx<R> *dC = tp + T;                                       // [nb][NT] diagonal-block thread factors (of D^dagger)
     Cx<R> *dR = dC + nb * blockDim.x;                         // [nb][16] register tables
     uint64_t *hioff = reinterpret_cast<uint64_t *>(dR + nb * 16);
     double *acc = reinterpret_cast<double *>(hioff + nh);
@@ -965,15 +964,10 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
     const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-    if (PREF) {
-        if (mine > 0) load_tile_async<R>(tps, psi, deposit(blockIdx.x, a.out, a.nout), hioff, a.nlow, T);
-        cp_async_commit();
-    }
     for (uint64_t it = 0; it < mine; ++it) {
         const uint64_t ti = blockIdx.x + it * gridDim.x;
         const uint64_t gbase = deposit(ti, a.out, a.nout);
-        Cx<R> *tp = tps + (PREF ? (it & 1) * T : 0);
-        if (!PREF && it + 1 < mine) {
+        if (it + 1 < mine) {
             // the next tile's psi and lambda runs head for L2 while this one is processed
             const uint64_t gn = deposit(ti + gridDim.x, a.out, a.nout);
             const uint32_t runbytes = (1u << a.nlow) * (uint32_t)sizeof(Cx<R>);
@@ -982,18 +976,11 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                 prefetch_l2(lam + (gn | hioff[j]), runbytes);
             }
         }
-        if (PREF) {
-            if (it + 1 < mine)
-                load_tile_async<R>(tps + ((it + 1) & 1) * T, psi, deposit(ti + gridDim.x, a.out, a.nout), hioff,
-                                   a.nlow, T);
-            cp_async_commit();
-        }
         for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
             const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
-            if (!PREF) tp[swz_tile(j)] = psi[gi];
+            tp[swz_tile(j)] = psi[gi];
             tl[swz_tile(j)] = lam[gi];
         }
-        if (PREF) cp_async_wait1();
         __syncthreads();
         for (int ph = a.ph_end - 1; ph >= a.ph_begin; --ph) {
             const Phase P = phases[ph];
@@ -2321,23 +2308,13 @@ cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, co
     const size_t nb = (size_t)(a.db_end - a.db_begin);
     const size_t rest = ((size_t)1 << (a.k - a.nlow)) * 8 + (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) +
                         nb * (512 + 16) * sizeof(Cx<R>) + nb * 512 * 2 + 64;
-    const bool pref = false;   // measured slower than loading psi and lambda together
-    (void)pref;
-    const size_t sm = (pref ? 3 : 2) * tile + rest;
+    const size_t sm = 2 * tile + rest;
     switch (a.k - 9) {
 #define SV_AR(RB)                                                                                            \
     case RB:                                                                                                 \
-        if (pref) {                                                                                          \
-            allow_smem(k_adj_reg<R, RB, true>, sm);                                                          \
-            k_adj_reg<R, RB, true><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases,        \
-                                                          (const R *)coef, (const Cx<R> *)mats, part,        \
-                                                          part_stride, dblocks, dmem);                       \
-        } else {                                                                                             \
-            allow_smem(k_adj_reg<R, RB, false>, sm);                                                         \
-            k_adj_reg<R, RB, false><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases,       \
-                                                           (const R *)coef, (const Cx<R> *)mats, part,       \
-                                                           part_stride, dblocks, dmem);                      \
-        }                                                                                                    \
+        allow_smem(k_adj_reg<R, RB>, sm);                                                                    \
+        k_adj_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases, (const R *)coef, \
+                                                (const Cx<R> *)mats, part, part_stride, dblocks, dmem);      \
         break;
         SV_AR(2) SV_AR(3) SV_AR(4)
 #undef SV_AR
