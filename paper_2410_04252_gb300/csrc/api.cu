@@ -439,7 +439,8 @@ sv_status evc_entry_upload(sv_handle *h, EvcEntry *ent, const double *coeffs, si
         gs[i].X = g.X;
         gs[i].s_begin = g.s_begin;
         gs[i].s_end = g.s_end;
-        gs[i].pad = 0;
+        gs[i].parts = 0;
+        for (int32_t q = g.s_begin; q < g.s_end; ++q) gs[i].parts |= 1 << (ent->plan.strings[q].nY & 1);
     }
     std::vector<DevString> ss(ent->plan.strings.size());
     for (size_t i = 0; i < ss.size(); ++i) {
@@ -1294,7 +1295,8 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
         gs[i].X = H.groups[i].X;
         gs[i].s_begin = H.groups[i].s_begin;
         gs[i].s_end = H.groups[i].s_end;
-        gs[i].pad = 0;
+        gs[i].parts = 0;
+        for (int32_t q = H.groups[i].s_begin; q < H.groups[i].s_end; ++q) gs[i].parts |= 1 << (H.strings[q].nY & 1);
     }
     std::vector<DevString> ss(H.strings.size());
     for (size_t i = 0; i < ss.size(); ++i) {

@@ -50,6 +50,22 @@ __device__ __forceinline__ uint64_t deposit(uint64_t v, const int8_t *bits, int 
     return o;
 }
 
+// Stepping deposit(v) to deposit(v + stride) without re-depositing: with the
+// bit list ascending, deposit is an order-preserving embedding, so the sum is
+// the masked addition ((x | ~mask) + deposit(stride)) & mask (carries ripple
+// through the bits outside the mask).
+struct BitWalk {
+    uint64_t nmask, d;
+};
+__device__ __forceinline__ BitWalk bit_walk(const int8_t *bits, int nb, uint64_t stride) {
+    uint64_t m = 0;
+    for (int i = 0; i < nb; ++i) m |= 1ull << bits[i];
+    return {~m, deposit(stride, bits, nb)};
+}
+__device__ __forceinline__ uint64_t walk_next(uint64_t x, const BitWalk &w) {
+    return ((x | w.nmask) + w.d) & ~w.nmask;
+}
+
 template <typename R>
 __device__ __forceinline__ void rot(Cx<R> &u, Cx<R> &v, R c, R s) {
     const Cx<R> a = u, b = v;
@@ -519,6 +535,28 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Complex load from a 32-bit shared-window address (the coset loops compute
+// partner addresses as shared offsets, so no 64-bit pointer arithmetic).
+// Ordered against the barriers around it by being volatile.
+template <typename R> __device__ __forceinline__ Cx<R> lds_cx(uint32_t addr);
+template <> __device__ __forceinline__ Cx<float> lds_cx<float>(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+template <> __device__ __forceinline__ Cx<double> lds_cx<double>(uint32_t addr) {
+    double2 v;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr));
+    return v;
+}
+// The same for complex64 at addr + OFF (OFF a compile-time byte offset, so
+// the address is one register plus an immediate).
+template <int OFF> __device__ __forceinline__ float2 lds_f2_off(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(OFF));
+    return v;
+}
+
 // ------------------------------------------------- register-blocked passes --
 // A pass of RY / RZ / CZ / 1-qubit matrices runs in phases (host planned):
 // in a phase each of the 512 threads holds the 2^RB amplitudes spanned by
@@ -887,14 +925,17 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
     const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // tile bases walked with masked additions (current, and two ahead)
+    const BitWalk bw = bit_walk(a.out, a.nout, gridDim.x);
+    uint64_t base_pf = deposit(blockIdx.x, a.out, a.nout), base_cur = base_pf;
     for (uint64_t k = 0; k < 2; ++k) {
-        if (k < mine)
-            load_tile_async<R>(tiles + k * T, psi, deposit(blockIdx.x + k * gridDim.x, a.out, a.nout), hioff, a.nlow, T);
+        if (k < mine) load_tile_async<R>(tiles + k * T, psi, base_pf, hioff, a.nlow, T);
         cp_async_commit();
+        base_pf = walk_next(base_pf, bw);
     }
     for (uint64_t it = 0; it < mine; ++it) {
-        const uint64_t ti = blockIdx.x + it * gridDim.x;
-        const uint64_t gbase = deposit(ti, a.out, a.nout);
+        const uint64_t gbase = base_cur;
+        base_cur = walk_next(base_cur, bw);
         Cx<R> *tile = tiles + (it & 1) * T;
         cp_async_wait1();
         __syncthreads();
@@ -926,9 +967,9 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
         }
         for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = tile[swz_tile(j)];
         __syncthreads();
-        if (it + 2 < mine)
-            load_tile_async<R>(tile, psi, deposit(ti + 2 * gridDim.x, a.out, a.nout), hioff, a.nlow, T);
+        if (it + 2 < mine) load_tile_async<R>(tile, psi, base_pf, hioff, a.nlow, T);
         cp_async_commit();
+        base_pf = walk_next(base_pf, bw);
     }
 }
 
@@ -964,12 +1005,14 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
     const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const BitWalk bw = bit_walk(a.out, a.nout, gridDim.x);
+    uint64_t gnext = deposit(blockIdx.x, a.out, a.nout);
     for (uint64_t it = 0; it < mine; ++it) {
-        const uint64_t ti = blockIdx.x + it * gridDim.x;
-        const uint64_t gbase = deposit(ti, a.out, a.nout);
+        const uint64_t gbase = gnext;
+        gnext = walk_next(gnext, bw);
         if (it + 1 < mine) {
             // the next tile's psi and lambda runs head for L2 while this one is processed
-            const uint64_t gn = deposit(ti + gridDim.x, a.out, a.nout);
+            const uint64_t gn = gnext;
             const uint32_t runbytes = (1u << a.nlow) * (uint32_t)sizeof(Cx<R>);
             for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) {
                 prefetch_l2(psi + (gn | hioff[j]), runbytes);
@@ -1122,8 +1165,11 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
     const uint32_t runmask = (1u << a.L) - 1u;
     const uint64_t ntiles = 1ull << a.nout;
     const bool vec = (VEC == 2) && a.L >= 1;
+    const BitWalk bw = bit_walk(a.out, a.nout, gridDim.x);
+    uint64_t bnext = deposit(blockIdx.x, a.out, a.nout);
     for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-        const uint64_t b0 = deposit(ti, a.out, a.nout);
+        const uint64_t b0 = bnext;
+        bnext = walk_next(bnext, bw);
         const uint64_t b1 = sigma_hi(b0, a);
         if (b1 < b0) continue;
         const bool self = (b1 == b0);
@@ -1302,73 +1348,138 @@ __device__ __forceinline__ double flip_bit(double v, uint32_t sm) {
     return __longlong_as_double(__double_as_longlong(v) ^ ((long long)((sm >> J) & 1u) << 63));
 }
 
+// +1 or -1 by bit i of w.
+template <typename R>
+__device__ __forceinline__ R sign_of_bit(uint32_t w, int i) {
+    return ((w >> i) & 1u) ? (R)-1 : (R)1;
+}
+
+// sum_j (-1)^{parity(j & w)} val[j] over N = 2^L values, as the Walsh-Hadamard
+// butterfly restricted to one output: level i folds pairs differing in bit i
+// with one fused multiply-add by the sign of bit i of w (log2 N levels, N - 1
+// operations, no per-element sign work).
+template <typename R, int N>
+__device__ __forceinline__ R walsh_sum(R *val, uint32_t w) {
+#pragma unroll
+    for (int i = 0, n = N; n > 1; ++i, n >>= 1) {
+        const R sg = sign_of_bit<R>(w, i);
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) val[k] = fma(sg, val[2 * k + 1], val[2 * k]);
+    }
+    return val[0];
+}
+
 // Sum over the selected elements j = (j' with bit S inserted at H) of the
-// pair term Re or Im(conj(partner) own), signed by sm.  NT = 2^LOGNT, E = EPT*NT.
+// pair term Re or Im(conj(partner) own), signed by (-1)^{parity(j & w)}.
+// NT = 2^LOGNT, E = EPT*NT.
 template <typename R, int EPT, int H, int S, bool ODD, int LOGNT>
-__device__ __forceinline__ R evc_sel_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
+__device__ __forceinline__ R evc_sel_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t w) {
     constexpr int SH = LOGNT + (sizeof(R) == 4 ? 3 : 4);
-    R a0 = 0, a1 = 0;
+    R val[EPT / 2];
     // partner of element j: byte offset B ^ (j << SH) of the staged coset
-    const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(t);
+    const uint32_t sb = smem_u32(t);
     const uint32_t B = (threadIdx.x ^ X) * (uint32_t)sizeof(Cx<R>);
 #pragma unroll
     for (int jp = 0; jp < EPT / 2; ++jp) {
         const int j = ((jp >> H) << (H + 1)) | (S << H) | (jp & ((1 << H) - 1));
         const Cx<R> u = own[j];
-        const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
-        const R val = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
-        R f;
-        switch (j) {   // compile-time after unrolling
-#define SV_FB(J) case J: f = flip_bit<J>(val, sm); break;
-            SV_FB(0) SV_FB(1) SV_FB(2) SV_FB(3) SV_FB(4) SV_FB(5) SV_FB(6) SV_FB(7)
-            SV_FB(8) SV_FB(9) SV_FB(10) SV_FB(11) SV_FB(12) SV_FB(13) SV_FB(14) SV_FB(15)
-#undef SV_FB
-        default: f = val; break;
-        }
-        if (jp & 1) a1 += f; else a0 += f;
+        const Cx<R> v = lds_cx<R>(sb + (B ^ ((uint32_t)j << SH)));
+        val[jp] = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
     }
-    return a0 + a1;
+    // parity(j & w) = (S & w_H) ^ parity(j' & w'), w' = w with bit H removed
+    const uint32_t wp = (w & ((1u << H) - 1u)) | ((w >> (H + 1)) << H);
+    const R r = walsh_sum<R, EPT / 2>(val, wp);
+    return (S && ((w >> H) & 1u)) ? -r : r;
 }
 
 template <typename R, int EPT, bool ODD, int LOGNT>
-__device__ __forceinline__ R evc_all_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t sm) {
+__device__ __forceinline__ R evc_all_loop(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t w) {
     constexpr int SH = LOGNT + (sizeof(R) == 4 ? 3 : 4);
-    R a0 = 0, a1 = 0;
-    const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(t);
+    R val[EPT];
+    const uint32_t sb = smem_u32(t);
     const uint32_t B = (threadIdx.x ^ X) * (uint32_t)sizeof(Cx<R>);
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
         const Cx<R> u = own[j];
-        const Cx<R> v = *reinterpret_cast<const Cx<R> *>(tbytes + (B ^ ((uint32_t)j << SH)));
-        const R val = X ? (ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y)) : (u.x * u.x + u.y * u.y);
-        const R f = ((sm >> j) & 1u) ? -val : val;
-        if (j & 1) a1 += f; else a0 += f;
+        if (X) {
+            const Cx<R> v = lds_cx<R>(sb + (B ^ ((uint32_t)j << SH)));
+            val[j] = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
+        } else {
+            val[j] = u.x * u.x + u.y * u.y;
+        }
     }
-    return a0 + a1;
+    return walsh_sum<R, EPT>(val, w);
 }
 
-// Fast path (NT = 2^LOGNT, E = EPT * NT): dispatch on (h, s, odd).
-template <typename R, int EPT, bool ODD, int LOGNT>
-__device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t X, PairSel ps, uint32_t sm) {
-    if (ps.h < 0) return evc_all_loop<R, EPT, ODD, LOGNT>(t, own, X, sm);
-#define SV_SEL(HH)                                                                                       \
-    if (ps.h == HH) {                                                                                    \
-        if constexpr ((1 << (HH + 1)) <= EPT) {                                                          \
-            return ps.s ? evc_sel_loop<R, EPT, HH, 1, ODD, LOGNT>(t, own, X, sm)                                \
-                        : evc_sel_loop<R, EPT, HH, 0, ODD, LOGNT>(t, own, X, sm);                               \
-        }                                                                                                \
-    }
-    SV_SEL(0) SV_SEL(1) SV_SEL(2) SV_SEL(3)
+// Fast path (NT = 2^LOGNT, E = EPT * NT): one switch on the pass code
+// (h + 1) | s << 3 | odd << 4 of the pair split (h = -1: every element); the
+// result is signed by (-1)^{parity(j & w)} per element j.
+template <typename R, int EPT, int LOGNT>
+__device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t X, uint32_t code, uint32_t w) {
+    switch (code) {
+    case 0: return evc_all_loop<R, EPT, false, LOGNT>(t, own, X, w);
+    case 16: return evc_all_loop<R, EPT, true, LOGNT>(t, own, X, w);
+#define SV_SEL(HH, SS, OO)                                                                               \
+    case (HH + 1) | (SS << 3) | (OO << 4):                                                               \
+        if constexpr ((1 << (HH + 1)) <= EPT) return evc_sel_loop<R, EPT, HH, SS, OO != 0, LOGNT>(t, own, X, w); \
+        else return (R)0;
+#define SV_SEL4(HH) SV_SEL(HH, 0, 0) SV_SEL(HH, 1, 0) SV_SEL(HH, 0, 1) SV_SEL(HH, 1, 1)
+    SV_SEL4(0) SV_SEL4(1) SV_SEL4(2) SV_SEL4(3)
+#undef SV_SEL4
 #undef SV_SEL
-    return (R)0;
+    default: return (R)0;
+    }
+}
+
+// Large groups (complex64, 16 amplitudes per thread, 512 threads, 8192
+// staged): instead of a signed sum per string, the coset's pair terms
+// val(b) = Re or Im of conj(psi[b^x]) psi[b] (every b, each pair from both
+// sides) are Walsh-Hadamard transformed over the element bits (in registers)
+// and the lane bits (shuffles); the 16 warps' partial transforms go to
+// shared memory, and the thread owning string s finishes its one
+// coefficient with a 16-term signed sum over the warp bits.  Because
+// parity(b & z) = parity(rep & z) ^ parity(t & tau) ^ parity(j & w) with
+// tau = (z mod 2^kl) | (bz mod 2^ash) << kl, string s needs the coefficient
+// at element frequency w, lane frequency tau mod 32 and warp frequency
+// tau >> 5.  Cost per coset: one transform per group and needed part (Re,
+// Im), independent of the group's string count.
+constexpr int kXformMinStrings = 6;   // groups with at least this many strings take the transform path
+constexpr int kXformScratch = 8192;   // floats of shared scratch (16 element x 16 warp x 32 lane frequencies)
+
+__device__ __forceinline__ void xform_part(float *v, float *scr, const float *lsg) {
+    // element bits: in-register butterflies (natural-order output)
+#pragma unroll
+    for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (!(i & h)) {
+                const float x = v[i], y = v[i + h];
+                v[i] = x + y;
+                v[i + h] = x - y;
+            }
+    // lane bits: the lower lane of a pair keeps x + y, the upper y - x... as fma(sign, own, partner)
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaf(lsg[b], v[i], __shfl_xor_sync(0xffffffffu, v[i], 1 << b));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) scr[(i * 16 + warp) * 32 + lane] = v[i];
+}
+
+// Owner side: coefficient (fj, fw, fl) of the scratch, finished over the warp bits.
+__device__ __forceinline__ float xform_coef(const float *scr, uint32_t fj, uint32_t fw, uint32_t fl) {
+    float c[16];
+#pragma unroll
+    for (int w = 0; w < 16; ++w) c[w] = scr[(fj * 16 + w) * 32 + fl];
+    return walsh_sum<float, 16>(c, fw);
 }
 
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                      const DevGroup *__restrict__ groups,
                                                      const DevString *__restrict__ strs, double *__restrict__ part,
-                                                     int part_stride, int *status, long long limit) {
-    (void)status; (void)limit;
+                                                     int part_stride, int xform) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t E = 1u << (a.kl + a.m);
     const int nslots = a.s_end - a.s_begin;
@@ -1376,18 +1487,31 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
     Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
     uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
     double *acc = reinterpret_cast<double *>(spanv + (1u << a.m));
+    float *scr = reinterpret_cast<float *>(acc + nslots * nwarps);     // transform scratch (when xform)
     for (int j = threadIdx.x; j < nslots * nwarps; j += blockDim.x) acc[j] = 0.0;
     coset_span(a, spanv);
     const ThreadCoset tc = thread_coset(a.kl);
+    // the transform path needs complex64, 16 per thread, 512 threads, 8192 staged, the scratch
+    bool use_x = false;
+    float lsg[5] = {1.f, 1.f, 1.f, 1.f, 1.f};
+    if constexpr (sizeof(R) == 4 && EPT == 16) {
+        use_x = xform && blockDim.x == 512 && E == 8192u;
+        for (int b = 0; b < 5; ++b) lsg[b] = ((lane >> b) & 1) ? -1.f : 1.f;
+    }
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    // coset representatives walked with masked additions: rep_cur of the
+    // current iteration, rep_pf of the one two ahead (the next copy issued)
+    const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
+    uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
     for (uint64_t k = 0; k < 2; ++k) {
-        if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        if (k < mine) load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
     }
     for (uint64_t it = 0; it < mine; ++it) {
-        const uint64_t ci = blockIdx.x + it * gridDim.x;
-        const uint64_t rep = deposit(ci, a.freeb, a.nfree);
+        const uint64_t rep = rep_cur;
+        rep_cur = walk_next(rep_cur, bw);
         Cx<R> *t = buf + (it & 1) * E;
         cp_async_wait1();
         __syncthreads();
@@ -1399,6 +1523,37 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
         }
         for (int gi = a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
+            if constexpr (sizeof(R) == 4 && EPT == 16) {
+                if (use_x && G.s_end - G.s_begin >= kXformMinStrings) {
+                    for (int part_i = 0; part_i < 2; ++part_i) {
+                        if (!((G.parts >> part_i) & 1)) continue;   // no string uses this part
+                        float v[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const Cx<R> u = own[j];
+                            if (G.X) {
+                                const Cx<R> w = t[(threadIdx.x + j * 512u) ^ G.X];
+                                v[j] = part_i ? (w.x * u.y - w.y * u.x) : (w.x * u.x + w.y * u.y);
+                            } else {
+                                v[j] = u.x * u.x + u.y * u.y;
+                            }
+                        }
+                        xform_part(v, scr, lsg);
+                        __syncthreads();
+                        for (int q = G.s_begin + (int)threadIdx.x; q < G.s_end; q += 512) {
+                            const DevString S = strs[q];
+                            if ((S.nY & 1) != part_i) continue;
+                            const uint32_t tau = (uint32_t)(S.z & ((1ull << a.kl) - 1ull)) |
+                                                 ((S.bz & ((1u << tc.ash) - 1u)) << a.kl);
+                            float c = xform_coef(scr, (S.bz >> tc.ash) & 15u, tau >> 5, tau & 31u);
+                            const int neg = (__popcll(rep & S.z) ^ (G.X ? ((S.nY == 1) | (S.nY == 2)) : 0)) & 1;
+                            acc[(q - a.s_begin) * nwarps] += (double)(neg ? -c : c);
+                        }
+                        __syncthreads();
+                    }
+                    continue;
+                }
+            }
             int ifac = 1;
             const uint32_t sel = G.X ? pair_select(tc, G.X, a.kl, EPT, ifac) : 0xFFFFFFFFu;
             const R fac = (R)ifac;
@@ -1448,8 +1603,9 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
             }
         }
         __syncthreads();
-        if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        if (it + 2 < mine) load_coset<R>(t, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
     }
     __syncthreads();
     for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
@@ -1492,15 +1648,16 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restri
     Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
     uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
     R *acc32 = reinterpret_cast<R *>(spanv + (1u << a.m));             // [ng][NT], the state's real type
-    uint32_t *pg = reinterpret_cast<uint32_t *>(acc32 + kEvcFew * NT);  // [ng][NT]: sel | tconst << 31
+    uint32_t *pg = reinterpret_cast<uint32_t *>(acc32 + kEvcFew * NT);  // [ng][NT]: sel | code << 16 | tconst << 31
     __shared__ uint64_t gz[kEvcFew];
-    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew];
+    __shared__ uint32_t gX[kEvcFew], gjm[kEvcFew], gw[kEvcFew];
     __shared__ int gmeta[kEvcFew];                                      // odd | fac << 1
     __shared__ double wsum[kEvcFew][32];                                // FP64 per string and warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int j = threadIdx.x; j < kEvcFew * 32; j += NT) wsum[j / 32][j % 32] = 0.0;
     coset_span(a, spanv);
     const ThreadCoset tc = thread_coset(a.kl);
+    uint32_t tmask = 0;                                                 // bit g: sign constant of group g
     for (int g = 0; g < ng; ++g) {
         const DevGroup G = groups[a.g_begin + g];
         const DevString S = strs[G.s_begin];
@@ -1509,15 +1666,17 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restri
         const int neg0 = G.X ? ((S.nY == 1) | (S.nY == 2)) : 0;
         const int tconst = (__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ neg0) & 1;
         const PairSel ps = G.X ? pair_split(tc, G.X, a.kl, EPT) : PairSel{-1, 0, 1};
-        // packed: sel (bits 0..15), split bit h + 1 (bits 16..19, 0 = every element),
-        // side s (bit 20), sign constant (bit 31)
-        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | ((uint32_t)(ps.h + 1) << 16) | ((uint32_t)ps.s << 20) |
-                                   ((uint32_t)tconst << 31);
+        // packed: sel (bits 0..15), fast-path code (h + 1) | s << 3 | odd << 4
+        // (bits 16..20, h + 1 = 0: every element), sign constant (bit 31)
+        const uint32_t code = (uint32_t)(ps.h + 1) | ((uint32_t)ps.s << 3) | ((uint32_t)(S.nY & 1) << 4);
+        pg[g * NT + threadIdx.x] = (sel & 0xFFFFu) | (code << 16) | ((uint32_t)tconst << 31);
+        tmask |= (uint32_t)tconst << g;
         acc32[g * NT + threadIdx.x] = (R)0;
         if (threadIdx.x == 0) {
             gz[g] = S.z;
             gX[g] = G.X;
             gjm[g] = walsh_mask(S.bz >> tc.ash);
+            gw[g] = S.bz >> tc.ash;
             gmeta[g] = (S.nY & 1) | (fac << 1);
         }
     }
@@ -1525,13 +1684,18 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restri
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const bool fast = (NT == (1 << LOGNT)) && (E == ((uint32_t)EPT << LOGNT)) && EPT >= 2;
+    // coset representatives walked with masked additions: rep_cur of the
+    // current iteration, rep_pf of the one two ahead (the next copy issued)
+    const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
+    uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
     for (uint64_t k = 0; k < 2; ++k) {
-        if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        if (k < mine) load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
     }
     for (uint64_t it = 0; it < mine; ++it) {
-        const uint64_t ci = blockIdx.x + it * gridDim.x;
-        const uint64_t rep = deposit(ci, a.freeb, a.nfree);
+        const uint64_t rep = rep_cur;
+        rep_cur = walk_next(rep_cur, bw);
         Cx<R> *t = buf + (it & 1) * E;
         cp_async_wait1();
         __syncthreads();
@@ -1541,18 +1705,19 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restri
             const uint32_t e = threadIdx.x + j * blockDim.x;
             own[j] = e < E ? t[e] : mk<R>(0, 0);
         }
+        // bit g: parity(rep & z_g) of every group at once (lane g computes it)
+        const uint32_t bmask =
+            tmask ^ __ballot_sync(0xffffffffu, lane < ng && ((__popcll(rep & gz[lane < ng ? lane : 0]) & 1) != 0));
         for (int g = 0; g < ng; ++g) {
             const uint32_t p = pg[g * NT + threadIdx.x];
             const uint32_t X = gX[g];
             const int meta = gmeta[g];
-            const int base = ((int)(p >> 31) ^ __popcll(rep & gz[g])) & 1;
+            const int base = (bmask >> g) & 1;
             const uint32_t sel = X ? (p & 0xFFFFu) : 0xFFFFFFFFu;
             R v;
             if (fast) {
-                const uint32_t sm = base ? ~gjm[g] : gjm[g];
-                const PairSel ps{(int)((p >> 16) & 15u) - 1, (int)((p >> 20) & 1u), 0};
-                v = (meta & 1) ? evc_fast<R, EPT, true, LOGNT>(t, own, X, ps, sm)
-                               : evc_fast<R, EPT, false, LOGNT>(t, own, X, ps, sm);
+                v = evc_fast<R, EPT, LOGNT>(t, own, X, (p >> 16) & 31u, gw[g]);
+                if (base) v = -v;
             } else if (X == 0u) {
                 v = 0;
 #pragma unroll
@@ -1567,20 +1732,21 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restri
             } else {
                 v = evc_pairs<R, EPT, false>(t, own, X, sel, base, gjm[g], E);
             }
-            acc32[g * NT + threadIdx.x] += v * (R)(meta >> 1);
+            acc32[g * NT + threadIdx.x] += v;
         }
         if ((it & 63) == 63 || it + 1 == mine) {
-            // flush: FP64 warp sums into the per-warp slots (fixed order)
+            // flush: FP64 warp sums (times the pair factor) into the per-warp slots (fixed order)
             for (int g = 0; g < ng; ++g) {
-                double v = (double)acc32[g * NT + threadIdx.x];
+                double v = (double)acc32[g * NT + threadIdx.x] * (double)(gmeta[g] >> 1);
                 acc32[g * NT + threadIdx.x] = (R)0;
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) wsum[g][warp] += v;
             }
         }
         __syncthreads();
-        if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        if (it + 2 < mine) load_coset<R>(t, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
     }
     __syncthreads();
     if (threadIdx.x < ng) {
@@ -1646,29 +1812,85 @@ __device__ __forceinline__ void hpsi_fast(Cx<R> *acc, const Cx<R> *t, uint32_t X
 // complex64, 16 amplitudes per thread (NT = 512, E = 8192): the signed
 // coefficient of element j is built along a Gray chain written out (each
 // one XOR from an earlier one), and the partner of element j is at byte
-// offset B ^ (j << 12) of the staged coset (B = (t ^ X) * 8).
+// offset B ^ (j << 12) of the staged coset (B = (t ^ X) * 8) whose shared
+// address is sb.
 template <bool ODD>
-__device__ __forceinline__ void hpsi_gray16(float2 *acc, const unsigned char *tb, uint32_t B, uint32_t g0,
-                                            uint32_t w) {
+__device__ __forceinline__ void hpsi_gray16(float2 *acc, uint32_t sb, uint32_t B, uint32_t g0, uint32_t w) {
     const uint32_t F0 = (w & 1u) << 31, F1 = (w & 2u) << 30, F2 = (w & 4u) << 29, F3 = (w & 8u) << 28;
     const uint32_t g1 = g0 ^ F0, g2 = g0 ^ F1, g3 = g2 ^ F0, g4 = g0 ^ F2, g5 = g4 ^ F0, g6 = g4 ^ F1,
                    g7 = g6 ^ F0, g8 = g0 ^ F3, g9 = g8 ^ F0, g10 = g8 ^ F1, g11 = g10 ^ F0, g12 = g8 ^ F2,
                    g13 = g12 ^ F0, g14 = g12 ^ F1, g15 = g14 ^ F0;
 #define SV_HG(J)                                                                                 \
     {                                                                                            \
-        const float2 v = *reinterpret_cast<const float2 *>(tb + (B ^ ((uint32_t)(J) << 12)));   \
+        const float2 v = lds_cx<float>(sb + (B ^ ((uint32_t)(J) << 12)));                        \
         const float f = __uint_as_float(g##J);                                                   \
         if (ODD) {                                                                               \
-            acc[J].x -= f * v.y;                                                                 \
-            acc[J].y += f * v.x;                                                                 \
+            acc[J].x = fmaf(-f, v.y, acc[J].x);                                                  \
+            acc[J].y = fmaf(f, v.x, acc[J].y);                                                   \
         } else {                                                                                 \
-            acc[J].x += f * v.x;                                                                 \
-            acc[J].y += f * v.y;                                                                 \
+            acc[J].x = fmaf(f, v.x, acc[J].x);                                                   \
+            acc[J].y = fmaf(f, v.y, acc[J].y);                                                   \
         }                                                                                        \
     }
     SV_HG(0) SV_HG(1) SV_HG(2) SV_HG(3) SV_HG(4) SV_HG(5) SV_HG(6) SV_HG(7)
     SV_HG(8) SV_HG(9) SV_HG(10) SV_HG(11) SV_HG(12) SV_HG(13) SV_HG(14) SV_HG(15)
 #undef SV_HG
+}
+
+// hpsi_gray16 with the partner's row offset XH = (X >> 9) fixed at compile
+// time: the partner of element j is at Bl + ((j ^ XH) << 12), Bl = shared
+// address of the coset + (t ^ (X & 511)) * 8, so every load is one register
+// plus an immediate (rows 8..15 from Bl + 32 KiB, keeping immediates small).
+template <bool ODD, int XH>
+__device__ __forceinline__ void hpsi_row16(float2 *acc, uint32_t Bl, uint32_t g0, uint32_t w) {
+    const uint32_t Bh = Bl + 32768u;
+    const uint32_t F0 = (w & 1u) << 31, F1 = (w & 2u) << 30, F2 = (w & 4u) << 29, F3 = (w & 8u) << 28;
+    const uint32_t g1 = g0 ^ F0, g2 = g0 ^ F1, g3 = g2 ^ F0, g4 = g0 ^ F2, g5 = g4 ^ F0, g6 = g4 ^ F1,
+                   g7 = g6 ^ F0, g8 = g0 ^ F3, g9 = g8 ^ F0, g10 = g8 ^ F1, g11 = g10 ^ F0, g12 = g8 ^ F2,
+                   g13 = g12 ^ F0, g14 = g12 ^ F1, g15 = g14 ^ F0;
+#define SV_HR(J)                                                                                 \
+    {                                                                                            \
+        const float2 v = (((J) ^ XH) < 8) ? lds_f2_off<(((J) ^ XH) & 7) << 12>(Bl)               \
+                                          : lds_f2_off<(((J) ^ XH) & 7) << 12>(Bh);              \
+        const float f = __uint_as_float(g##J);                                                   \
+        if (ODD) {                                                                               \
+            acc[J].x = fmaf(-f, v.y, acc[J].x);                                                  \
+            acc[J].y = fmaf(f, v.x, acc[J].y);                                                   \
+        } else {                                                                                 \
+            acc[J].x = fmaf(f, v.x, acc[J].x);                                                   \
+            acc[J].y = fmaf(f, v.y, acc[J].y);                                                   \
+        }                                                                                        \
+    }
+    SV_HR(0) SV_HR(1) SV_HR(2) SV_HR(3) SV_HR(4) SV_HR(5) SV_HR(6) SV_HR(7)
+    SV_HR(8) SV_HR(9) SV_HR(10) SV_HR(11) SV_HR(12) SV_HR(13) SV_HR(14) SV_HR(15)
+#undef SV_HR
+}
+
+// Strings of one H|psi> pass staged once per launch (complex64, 16 amplitudes
+// per thread, 512 threads, at most kHpsiTab strings): per string the signed
+// coefficient, X (bit 31: nY odd), w and z; per thread the coset-independent
+// sign bits parity(l & z) ^ parity(a0 & bz) ^ nY of every string.  Per coset
+// one ballot gives parity(rep & z) of every string.
+constexpr int kHpsiTab = 32;
+struct HpsiTab {
+    uint64_t z[kHpsiTab];
+    uint32_t X[kHpsiTab], g[kHpsiTab], w[kHpsiTab];
+};
+
+__device__ __forceinline__ void hpsi_tab_string(float2 *acc, const HpsiTab &T, int k, uint32_t sb, uint32_t bmask) {
+    const uint32_t Xo = T.X[k];
+    const uint32_t g0 = T.g[k] ^ (((bmask >> k) & 1u) << 31);
+    const uint32_t w = T.w[k];
+    const uint32_t Bl = sb + ((threadIdx.x ^ (Xo & 511u)) << 3);
+    switch (((Xo >> 9) & 15u) | ((Xo >> 31) << 4)) {
+#define SV_HC(C) case C: hpsi_row16<((C) >> 4) != 0, (C) & 15>(acc, Bl, g0, w); break;
+        SV_HC(0) SV_HC(1) SV_HC(2) SV_HC(3) SV_HC(4) SV_HC(5) SV_HC(6) SV_HC(7)
+        SV_HC(8) SV_HC(9) SV_HC(10) SV_HC(11) SV_HC(12) SV_HC(13) SV_HC(14) SV_HC(15)
+        SV_HC(16) SV_HC(17) SV_HC(18) SV_HC(19) SV_HC(20) SV_HC(21) SV_HC(22) SV_HC(23)
+        SV_HC(24) SV_HC(25) SV_HC(26) SV_HC(27) SV_HC(28) SV_HC(29) SV_HC(30) SV_HC(31)
+#undef SV_HC
+    default: break;
+    }
 }
 
 template <typename R, int EPT>
@@ -1688,14 +1910,45 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const bool fast = (blockDim.x == 512) && (E == (uint32_t)EPT * 512u);
+    // coset representatives walked with masked additions: rep_cur of the
+    // current iteration, rep_pf of the one two ahead (the next copy issued)
+    const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
+    uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
     for (uint64_t k = 0; k < 2; ++k) {
-        if (k < mine) load_coset<R>(buf + k * E, psi, deposit(blockIdx.x + k * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        if (k < mine) load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
     }
+    // string table (complex64, 16 per thread, 512 threads, few strings)
+    __shared__ HpsiTab tabs;
+    int ns = 0;
+    uint32_t tmask = 0;
+    if constexpr (sizeof(R) == 4 && EPT == 16) {
+        if (fast) {
+            for (int gi = a.g_begin; gi < a.g_end; ++gi) {
+                const DevGroup G = groups[gi];
+                for (int sidx = G.s_begin; sidx < G.s_end; ++sidx, ++ns) {
+                    if (ns >= kHpsiTab) continue;
+                    const DevString S = strs[sidx];
+                    tmask |= (uint32_t)((__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1) << ns;
+                    if (threadIdx.x == 0) {
+                        const float g = (S.nY & 2) ? -(float)S.coef : (float)S.coef;
+                        tabs.z[ns] = S.z;
+                        tabs.X[ns] = G.X | ((uint32_t)(S.nY & 1) << 31);
+                        tabs.g[ns] = __float_as_uint(g);
+                        tabs.w[ns] = S.bz >> tc.ash;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const bool tabbed = ns > 0 && ns <= kHpsiTab;
+    const int lane = threadIdx.x & 31;
     double eacc = 0.0;
     for (uint64_t it = 0; it < mine; ++it) {
-        const uint64_t ci = blockIdx.x + it * gridDim.x;
-        const uint64_t rep = deposit(ci, a.freeb, a.nfree);
+        const uint64_t rep = rep_cur;
+        rep_cur = walk_next(rep_cur, bw);
         Cx<R> *t = buf + (it & 1) * E;
         Cx<R> acc[EPT], old[EPT];
 #pragma unroll
@@ -1707,7 +1960,16 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
         }
         cp_async_wait1();
         __syncthreads();
-        for (int gi = a.g_begin; gi < a.g_end; ++gi) {
+        if constexpr (sizeof(R) == 4 && EPT == 16) {
+            if (tabbed) {
+                const bool pb = lane < ns && ((__popcll(rep & tabs.z[lane < ns ? lane : 0]) & 1) != 0);
+                const uint32_t bmask = tmask ^ __ballot_sync(0xffffffffu, pb);
+                const uint32_t sb = smem_u32(t);
+                for (int k = 0; k < ns; ++k)
+                    hpsi_tab_string(reinterpret_cast<float2 *>(acc), tabs, k, sb, bmask);
+            }
+        }
+        for (int gi = tabbed ? a.g_end : a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
             for (int s = G.s_begin; s < G.s_end; ++s) {
                 const DevString S = strs[s];
@@ -1717,9 +1979,8 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
                     if (fast) {
                         const uint32_t g0 = __float_as_uint((float)g) ^ ((uint32_t)base << 31);
                         const uint32_t B = (threadIdx.x ^ G.X) * 8u;
-                        const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(t);
-                        if (S.nY & 1) hpsi_gray16<true>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
-                        else hpsi_gray16<false>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                        if (S.nY & 1) hpsi_gray16<true>(reinterpret_cast<float2 *>(acc), smem_u32(t), B, g0, S.bz >> tc.ash);
+                        else hpsi_gray16<false>(reinterpret_cast<float2 *>(acc), smem_u32(t), B, g0, S.bz >> tc.ash);
                         continue;
                     }
                 }
@@ -1750,8 +2011,9 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
         }
         eacc += (double)eloc;
         __syncthreads();
-        if (it + 2 < mine) load_coset<R>(t, psi, deposit(ci + 2 * gridDim.x, a.freeb, a.nfree), spanv, a.kl, E);
+        if (it + 2 < mine) load_coset<R>(t, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
     }
     if (last) {
         double v = eacc;
@@ -1963,11 +2225,11 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                             if (fast) {
                                 const uint32_t g0 = __float_as_uint((float)g) ^ ((uint32_t)base << 31);
                                 const uint32_t B = (threadIdx.x ^ G.X) * 8u;
-                                const unsigned char *tbytes = reinterpret_cast<const unsigned char *>(cur);
+                                const uint32_t sb = smem_u32(cur);
                                 if (S.nY & 1)
-                                    hpsi_gray16<true>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                                    hpsi_gray16<true>(reinterpret_cast<float2 *>(acc), sb, B, g0, S.bz >> tc.ash);
                                 else
-                                    hpsi_gray16<false>(reinterpret_cast<float2 *>(acc), tbytes, B, g0, S.bz >> tc.ash);
+                                    hpsi_gray16<false>(reinterpret_cast<float2 *>(acc), sb, B, g0, S.bz >> tc.ash);
                                 continue;
                             }
                         }
@@ -2187,6 +2449,15 @@ int occupancy(K kernel, int threads, size_t smem) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) nb = 1;
     return nb < 1 ? 1 : nb;
+}
+
+// Largest dynamic shared memory a block may opt in to on the current device.
+int smem_optin() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+        v = 48 * 1024;
+    return v;
 }
 
 template <typename K>
@@ -2447,12 +2718,18 @@ cudaError_t evc_dispatch(cudaStream_t st, int grid, const void *psi, const Coset
         }
 #undef SV_EVCF_CASE
     }
-    const size_t sm = coset_smem(sizeof(R) == 4 ? SV_C64 : SV_C128, E, a.m, a.s_end - a.s_begin, threads / 32);
+    size_t sm = coset_smem(sizeof(R) == 4 ? SV_C64 : SV_C128, E, a.m, a.s_end - a.s_begin, threads / 32);
+    // transform scratch for large groups (complex64, 16 per thread, 512 threads) when it fits
+    int xform = 0;
+    if (sizeof(R) == 4 && threads == 512 && E == 8192 && sm + kXformScratch * 4 <= (size_t)smem_optin()) {
+        sm += kXformScratch * 4;
+        xform = 1;
+    }
 #define SV_EVC_CASE(N)                                                                                       \
     case N:                                                                                                  \
         allow_smem(k_evc_pass<R, N>, sm);                                                                    \
         k_evc_pass<R, N><<<grid, threads, sm, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride, \
-                                                    status, limit);                                          \
+                                                    xform);                                                  \
         break;
     switch (ept) {
         SV_EVC_CASE(1)

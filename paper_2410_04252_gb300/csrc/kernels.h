@@ -33,7 +33,7 @@ struct DevGroup {
     uint64_t x;
     uint32_t X;
     int32_t s_begin, s_end;
-    int32_t pad;
+    int32_t parts;    // bit 0: a string with nY even (uses Re), bit 1: one with nY odd (uses Im)
 };
 struct DevString {
     uint64_t z;

@@ -109,7 +109,8 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
         gs[i].X = P.groups[i].X;
         gs[i].s_begin = P.groups[i].s_begin;
         gs[i].s_end = P.groups[i].s_end;
-        gs[i].pad = 0;
+        gs[i].parts = 0;
+        for (int32_t q = P.groups[i].s_begin; q < P.groups[i].s_end; ++q) gs[i].parts |= 1 << (P.strings[q].nY & 1);
     }
     std::vector<sv::DevString> ss(nslots);
     for (int i = 0; i < nslots; ++i) {

@@ -365,3 +365,38 @@ def test_diagonal_exemption_schedule(dtype, n, g, kinds):
     tol = 1e-4 * l1(h) if dtype == sv.C64 else 1e-7
     assert abs(e - ograd.objective(c, p, h, 5)) < tol
     assert np.max(np.abs(gr - ograd.finite_difference(c, p, h, 5))) < tol
+
+
+@pytest.mark.parametrize("sched", [sv.LAZY, sv.DIRECT])
+def test_evc_large_groups(sched):
+    """Groups of many strings sharing one x-mask (pure-Z terms, and X/Y masks
+    with many Z variants of both nY parities) on 8192-amplitude cosets: the
+    per-group transform path of the EVC pass, per term against the oracle."""
+    n, g = 17, 3
+    rng = np.random.default_rng(4242)
+    rows = []
+    for _ in range(70):                                   # pure Z, any weight, global qubits included
+        r = np.zeros(n, np.uint8)
+        r[rng.random(n) < 0.3] = 3
+        rows.append(r)
+    for size in (2, 3, 4):                                # three x-masks, 14 Z/Y variants each
+        xs = rng.choice(n - g, size, replace=False)
+        for _ in range(14):
+            r = np.zeros(n, np.uint8)
+            r[rng.random(n) < 0.4] = 3
+            r[xs] = rng.choice([1, 2], size)
+            rows.append(r)
+    for _ in range(20):                                   # scattered strings (single-string groups)
+        rows.append(rng.integers(0, 4, n).astype(np.uint8))
+    L = np.unique(np.array(rows), axis=0)
+    h = W.Hamiltonian(n, L, rng.normal(size=len(L)))
+    c = W.hea_circuit(n, 2)
+    params = W.uniform_params(c.nparams, 44, 0, 2 * math.pi)
+    psi = oracle_state(c, params, 0)
+    ref_terms = oracle.expect_terms(psi, h).real
+    s = sv.StateVector(n, g, sv.C64)
+    s.reset(0)
+    s.apply_circuit(c, params, sv.LAZY)
+    e, pt = s.expect(h, sched)
+    assert np.max(np.abs(pt - ref_terms)) < 2e-5
+    assert abs(e - float(np.dot(h.coeffs, ref_terms))) < 1e-4 * l1(h)
