@@ -1443,7 +1443,7 @@ __device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t
 // at element frequency w, lane frequency tau mod 32 and warp frequency
 // tau >> 5.  Cost per coset: one transform per group and needed part (Re,
 // Im), independent of the group's string count.
-constexpr int kXformMinStrings = 6;   // groups with at least this many strings take the transform path
+constexpr int kXformMinStrings = 16;  // groups with at least this many strings take the transform path
 constexpr int kXformScratch = 8192;   // floats of shared scratch (16 element x 16 warp x 32 lane frequencies)
 
 __device__ __forceinline__ void xform_part(float *v, float *scr, const float *lsg) {
@@ -1524,21 +1524,54 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
         for (int gi = a.g_begin; gi < a.g_end; ++gi) {
             const DevGroup G = groups[gi];
             if constexpr (sizeof(R) == 4 && EPT == 16) {
-                if (use_x && G.s_end - G.s_begin >= kXformMinStrings) {
+                const int K = G.s_end - G.s_begin;
+                if (use_x && K >= 2 && K < kXformMinStrings) {
+                    // a few strings: the pair terms of every element once, then per string a
+                    // Walsh fold over the element bits, the thread and coset signs, a warp sum
+                    float vr[16], vi[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const Cx<R> u = own[j];
+                        if (G.X) {
+                            const Cx<R> w = t[(threadIdx.x + j * 512u) ^ G.X];
+                            vr[j] = w.x * u.x + w.y * u.y;
+                            vi[j] = w.x * u.y - w.y * u.x;
+                        } else {
+                            vr[j] = u.x * u.x + u.y * u.y;
+                            vi[j] = 0.f;
+                        }
+                    }
+                    for (int q = G.s_begin; q < G.s_end; ++q) {
+                        const DevString S = strs[q];
+                        float f[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) f[j] = (S.nY & 1) ? vi[j] : vr[j];
+                        float c = walsh_sum<float, 16>(f, S.bz >> tc.ash);
+                        const int neg = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^
+                                         (G.X ? ((S.nY == 1) | (S.nY == 2)) : 0)) & 1;
+                        c = warp_sum<float>(neg ? -c : c);
+                        if (lane == 0) acc[(q - a.s_begin) * nwarps + warp] += (double)c;
+                    }
+                    continue;
+                }
+                if (use_x && K >= kXformMinStrings) {
+                    // both parts from one sweep over the partners
+                    float vr[16], vi[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const Cx<R> u = own[j];
+                        if (G.X) {
+                            const Cx<R> w = t[(threadIdx.x + j * 512u) ^ G.X];
+                            vr[j] = w.x * u.x + w.y * u.y;
+                            vi[j] = w.x * u.y - w.y * u.x;
+                        } else {
+                            vr[j] = u.x * u.x + u.y * u.y;
+                            vi[j] = 0.f;
+                        }
+                    }
                     for (int part_i = 0; part_i < 2; ++part_i) {
                         if (!((G.parts >> part_i) & 1)) continue;   // no string uses this part
-                        float v[16];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const Cx<R> u = own[j];
-                            if (G.X) {
-                                const Cx<R> w = t[(threadIdx.x + j * 512u) ^ G.X];
-                                v[j] = part_i ? (w.x * u.y - w.y * u.x) : (w.x * u.x + w.y * u.y);
-                            } else {
-                                v[j] = u.x * u.x + u.y * u.y;
-                            }
-                        }
-                        xform_part(v, scr, lsg);
+                        xform_part(part_i ? vi : vr, scr, lsg);
                         __syncthreads();
                         for (int q = G.s_begin + (int)threadIdx.x; q < G.s_end; q += 512) {
                             const DevString S = strs[q];

@@ -117,7 +117,8 @@ def test_qsu_edge_cases():
 
 @pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
 @pytest.mark.parametrize("sched", [sv.LAZY, sv.EAGER])
-@pytest.mark.parametrize("kind,n,g", [("random", 10, 2), ("random", 14, 3), ("jw", 12, 3), ("jw", 16, 4)])
+@pytest.mark.parametrize("kind,n,g", [("random", 10, 2), ("random", 14, 3), ("jw", 12, 3), ("jw", 16, 4),
+                                        ("random", 17, 3), ("jw", 17, 3)])
 def test_evc(dtype, sched, kind, n, g):
     h = W.random_hamiltonian(n, 64, 31 + n) if kind == "random" else W.jw_hamiltonian(n, 256, 33 + n)
     c = W.hea_circuit(n, 2)
