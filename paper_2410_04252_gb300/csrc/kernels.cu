@@ -86,17 +86,26 @@ __device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
     return a;
 }
-template <>
-__device__ __forceinline__ void rot<float>(float2 &u, float2 &v, float c, float s) {
+// the rotation with the coefficient pairs (c, c), (s, s), (-s, -s) already packed
+struct RotPairs {
+    unsigned long long C, S, NS;
+};
+__device__ __forceinline__ RotPairs rot_pairs(float c, float s) {
+    return {f2_pack(c, c), f2_pack(s, s), f2_pack(-s, -s)};
+}
+__device__ __forceinline__ void rot_packed(float2 &u, float2 &v, const RotPairs &k) {
     const unsigned long long U = f2_pack(u.x, u.y), V = f2_pack(v.x, v.y);
-    const unsigned long long C = f2_pack(c, c), S = f2_pack(s, s), NS = f2_pack(-s, -s);
     unsigned long long t, uu, vv;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(V), "l"(NS));
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(U), "l"(C), "l"(t));
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(V), "l"(C));
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(U), "l"(S), "l"(t));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(V), "l"(k.NS));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(U), "l"(k.C), "l"(t));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(V), "l"(k.C));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(U), "l"(k.S), "l"(t));
     u = f2_unpack(uu);
     v = f2_unpack(vv);
+}
+template <>
+__device__ __forceinline__ void rot<float>(float2 &u, float2 &v, float c, float s) {
+    rot_packed(u, v, rot_pairs(c, s));
 }
 
 template <typename R>
@@ -570,9 +579,16 @@ __device__ __forceinline__ uint32_t swz_tile(uint32_t i) {
 
 template <typename R, int V, int B>
 __device__ __forceinline__ void reg_rot(Cx<R> *x, R c, R s) {
+    if constexpr (sizeof(R) == 4) {
+        const RotPairs k = rot_pairs(c, s);   // once per gate, not per pair
 #pragma unroll
-    for (int v = 0; v < V; ++v)
-        if (!(v & (1 << B))) rot<R>(x[v], x[v | (1 << B)], c, s);
+        for (int v = 0; v < V; ++v)
+            if (!(v & (1 << B))) rot_packed(x[v], x[v | (1 << B)], k);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (!(v & (1 << B))) rot<R>(x[v], x[v | (1 << B)], c, s);
+    }
 }
 template <typename R, int V, int B>
 __device__ __forceinline__ void reg_mat1(Cx<R> *x, const Cx<R> *M, bool adj) {
@@ -717,14 +733,26 @@ __device__ __forceinline__ void reg_apply(Cx<R> *x, const DevOp &op, uint32_t rm
 template <typename R, int V, int B>
 __device__ __forceinline__ R reg_ry_adj(Cx<R> *p, Cx<R> *l, R c, R s) {
     R g = 0;
+    if constexpr (sizeof(R) == 4) {
+        const RotPairs k = rot_pairs(c, s);
 #pragma unroll
-    for (int v = 0; v < V; ++v)
-        if (!(v & (1 << B))) {
-            const int w = v | (1 << B);
-            g += (l[w].x * p[v].x + l[w].y * p[v].y) - (l[v].x * p[w].x + l[v].y * p[w].y);
-            rot<R>(p[v], p[w], c, s);
-            rot<R>(l[v], l[w], c, s);
-        }
+        for (int v = 0; v < V; ++v)
+            if (!(v & (1 << B))) {
+                const int w = v | (1 << B);
+                g += (l[w].x * p[v].x + l[w].y * p[v].y) - (l[v].x * p[w].x + l[v].y * p[w].y);
+                rot_packed(p[v], p[w], k);
+                rot_packed(l[v], l[w], k);
+            }
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (!(v & (1 << B))) {
+                const int w = v | (1 << B);
+                g += (l[w].x * p[v].x + l[w].y * p[v].y) - (l[v].x * p[w].x + l[v].y * p[w].y);
+                rot<R>(p[v], p[w], c, s);
+                rot<R>(l[v], l[w], c, s);
+            }
+    }
     return g;
 }
 template <typename R, int V, int B>
@@ -808,17 +836,34 @@ __device__ __forceinline__ void phase_index(uint32_t rmask, int k, uint32_t &bas
 // (cos, sin) of the half angle, so that a gate costs one shared load.
 template <typename R>
 struct StagedOp {
-    DevOp op;
     R c, s;
+    int32_t ry;    // 1 + register bit of an RY whose target is a register bit of its phase, else 0
+    int32_t pad;
+    DevOp op;
 };
 
+// Stages ops [begin, end) of a pass; phases [ph_begin, ph_end) give each op's
+// register set (rmask), so that the common RY case dispatches on one staged
+// field.
 template <typename R>
-__device__ __forceinline__ void stage_ops(StagedOp<R> *so, const DevOp *ops, int begin, int end, const R *coef) {
+__device__ __forceinline__ void stage_ops(StagedOp<R> *so, const DevOp *ops, int begin, int end, const R *coef,
+                                          const Phase *phases, int ph_begin, int ph_end) {
     for (int o = begin + threadIdx.x; o < end; o += blockDim.x) {
         StagedOp<R> x;
         x.op = ops[o];
         x.c = coef[2 * x.op.gate];
         x.s = coef[2 * x.op.gate + 1];
+        x.ry = 0;
+        x.pad = 0;
+        if (x.op.kind == SV_RY && x.op.t[0] >= 0 && x.op.t[0] < 32) {
+            for (int ph = ph_begin; ph < ph_end; ++ph) {
+                const Phase P = phases[ph];
+                if (o < P.op_begin || o >= P.op_end) continue;
+                const int t0 = x.op.t[0];
+                if ((P.rmask >> t0) & 1u) x.ry = 1 + __popc(P.rmask & ((1u << t0) - 1u));
+                break;
+            }
+        }
         so[o - begin] = x;
     }
 }
@@ -918,7 +963,7 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
     StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(hioff + nh);
     uint16_t *dM = reinterpret_cast<uint16_t *>(so + (a.op_end - a.op_begin));   // [nb][NT] CZ sign patterns
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
-    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
+    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef, phases, a.ph_begin, a.ph_end);
     __syncthreads();
     diag_setup<R, RB>(a, dblocks, dmem, so, dR, dC, dM, false);
     __syncthreads();
@@ -947,7 +992,19 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
 #pragma unroll
             for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
             for (int o = P.op_begin; o < P.op_end;) {
-                const StagedOp<R> x_op = so[o - a.op_begin];
+                const StagedOp<R> &x_op = so[o - a.op_begin];
+                if (x_op.ry > 0) {                   // RY on a register bit
+                    const R c = x_op.c, sn = x_op.s;
+                    switch (x_op.ry) {
+                    case 1: reg_rot<R, V, 0>(x, c, sn); break;
+                    case 2: if constexpr (RB > 1) reg_rot<R, V, 1>(x, c, sn); break;
+                    case 3: if constexpr (RB > 2) reg_rot<R, V, 2>(x, c, sn); break;
+                    case 4: if constexpr (RB > 3) reg_rot<R, V, 3>(x, c, sn); break;
+                    default: break;
+                    }
+                    ++o;
+                    continue;
+                }
                 DevOp op = x_op.op;
                 if (has_out_target(op)) op = resolve_out(op, gbase);
                 if (op.mat <= -2) {                  // a diagonal block: all its members at once
@@ -998,7 +1055,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     uint16_t *dM = reinterpret_cast<uint16_t *>(so + nops);                       // [nb][NT] CZ sign patterns
     for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
     for (int j = threadIdx.x; j < nops * nwarps; j += blockDim.x) acc[j] = 0.0;
-    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef);
+    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef, phases, a.ph_begin, a.ph_end);
     __syncthreads();
     diag_setup<R, RB>(a, dblocks, dmem, so, dR, dC, dM, true);
     __syncthreads();
@@ -1037,7 +1094,22 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                 xl[v] = tl[si];
             }
             for (int o = P.op_end - 1; o >= P.op_begin;) {
-                const StagedOp<R> x_op = so[o - a.op_begin];
+                const StagedOp<R> &x_op = so[o - a.op_begin];
+                if (x_op.ry > 0) {                   // RY on a register bit: gradient part, then RY^dagger
+                    const R c = x_op.c, sn = -x_op.s;
+                    R g = 0;
+                    switch (x_op.ry) {
+                    case 1: g = reg_ry_adj<R, V, 0>(xp, xl, c, sn); break;
+                    case 2: if constexpr (RB > 1) g = reg_ry_adj<R, V, 1>(xp, xl, c, sn); break;
+                    case 3: if constexpr (RB > 2) g = reg_ry_adj<R, V, 2>(xp, xl, c, sn); break;
+                    case 4: if constexpr (RB > 3) g = reg_ry_adj<R, V, 3>(xp, xl, c, sn); break;
+                    default: break;
+                    }
+                    g = warp_sum<R>(g);
+                    if (lane == 0) acc[(o - a.op_begin) * nwarps + warp] += (double)g;
+                    --o;
+                    continue;
+                }
                 DevOp op = x_op.op;
                 if (has_out_target(op)) op = resolve_out(op, gbase);
                 if (op.mat <= -2) {
