@@ -401,3 +401,21 @@ def test_evc_large_groups(sched):
     e, pt = s.expect(h, sched)
     assert np.max(np.abs(pt - ref_terms)) < 2e-5
     assert abs(e - float(np.dot(h.coeffs, ref_terms))) < 1e-4 * l1(h)
+
+
+@pytest.mark.parametrize("kind", ["random", "jw"])
+def test_adjoint_gradient_fast_coset_paths(kind):
+    """14 local qubits give 8192-amplitude cosets under the lazy schedule, the
+    shape of the n = 32 workload: the table-driven lambda = H psi pass (random
+    strings) and its general fallback (JW passes with many strings) inside
+    the gradient, against the parameter-shift rule."""
+    n, g = 17, 3
+    c = W.hea_circuit(n, 1)
+    params = W.uniform_params(c.nparams, 71, 0, 2 * math.pi)
+    h = W.random_hamiltonian(n, 48, 72) if kind == "random" else W.jw_hamiltonian(n, 120, 73)
+    s = sv.StateVector(n, g, sv.C64)
+    s.reset(0)
+    e, gr = s.grad(c, params, h, sv.LAZY)
+    tol = 1e-4 * l1(h)
+    assert abs(e - ograd.objective(c, params, h)) < tol
+    assert np.max(np.abs(gr - ograd.parameter_shift(c, params, h))) < tol
