@@ -95,8 +95,9 @@ cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, vo
 // In-place swap of disjoint physical bit pairs (pairs[2i], pairs[2i+1]).
 cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const int32_t *pairs,
                            int npairs, int blocks_per_sm);
-// Coset passes wait on bulk copies with bounded polls (limit); on expiry they
-// set *status = 1 and return early.
+// Coset passes.  Their copies complete by cp.async groups, so no pass spins;
+// status and limit are kept for the bounded-wait contract of the C ABI and
+// are not read by the current kernels.
 cudaError_t launch_evc_pass(sv_dtype dt, cudaStream_t st, int grid, const void *psi, const CosetArgs &a,
                             const DevGroup *groups, const DevString *strs, double *part, int part_stride,
                             int *status, long long limit);
