@@ -233,6 +233,18 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- ours --
 
+def reduce_times(dev_ms, wall_ms, steps, world, dist=None, device="cpu"):
+    """Max over ranks of the device and wall times of the timed region, then
+    the per-step time of one rank and the whole-job values (time per step of
+    the job = time / (steps x ranks), every rank running its own replica)."""
+    import torch
+    t = torch.tensor([dev_ms, wall_ms], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_ms, wall_ms = float(t[0]), float(t[1])
+    return dev_ms, wall_ms, dev_ms / steps, dev_ms / (steps * world), wall_ms / (steps * world)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -328,14 +340,8 @@ def run_ours(args):
     wall_ms = (time.perf_counter() - w0) * 1e3
     barrier()
     clk = clocks.stop()
-    dev_ms = ev0.elapsed_time(ev1)
-    tmax = torch.tensor([dev_ms, wall_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    dev_ms, wall_ms = float(tmax[0]), float(tmax[1])
-    ms_per_step = dev_ms / args.steps
-    value = dev_ms / (args.steps * world)
-    e2e_value = wall_ms / (args.steps * world)
+    dev_ms, wall_ms, ms_per_step, value, e2e_value = reduce_times(ev0.elapsed_time(ev1), wall_ms, args.steps,
+                                                                   world, dist, "cuda")
 
     # eager schedule on the same GPU (shorter run)
     eager = None

@@ -1,0 +1,52 @@
+"""The multi-rank timing path of bench.py on CPU: two gloo ranks (one process
+each, as torchrun starts them) reduce their timed-region lengths to the max
+over ranks, and the whole-job value counts every rank's replica."""
+import multiprocessing as mp
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        # rank r's timed region: 100 (r + 1) ms on the device, 150 + r ms of wall clock, 4 steps
+        q.put((rank,) + bench.reduce_times(100.0 * (rank + 1), 150.0 + rank, 4, world, dist, "cpu"))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_times_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, dev, wall, per_step, value, e2e in got:
+        assert dev == 200.0 and wall == 151.0          # max over the ranks, the same on every rank
+        assert per_step == 50.0                         # one rank's time per step
+        assert value == 25.0                            # 2 replicas x 4 steps in 200 ms
+        assert e2e == pytest.approx(151.0 / 8)
+
+
+def test_reduce_times_single_rank():
+    import bench
+    assert bench.reduce_times(90.0, 120.0, 3, 1) == (90.0, 120.0, 30.0, 30.0, 40.0)
