@@ -543,6 +543,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Complex load from a 32-bit shared-window address (the coset loops compute
 // partner addresses as shared offsets, so no 64-bit pointer arithmetic).
@@ -1247,12 +1248,15 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
         const bool self = (b1 == b0);
         if (self && a.nlo == 0) continue;
         if (vec) {
+            // 16-byte copies straight into shared memory (j even and bit 0 of b0, b1 clear: both ends aligned)
             for (uint32_t j = 2 * threadIdx.x; j < T; j += 2 * blockDim.x) {
                 const uint64_t off = hioff[j >> a.L] | (j & runmask);
                 const uint32_t s = swz<R>(j);
-                *reinterpret_cast<float4 *>(&A[s]) = *reinterpret_cast<const float4 *>(&psi[b0 | off]);
-                if (!self) *reinterpret_cast<float4 *>(&B[s]) = *reinterpret_cast<const float4 *>(&psi[b1 | off]);
+                cp_async16(&A[s], &psi[b0 | off]);
+                if (!self) cp_async16(&B[s], &psi[b1 | off]);
             }
+            cp_async_commit();
+            cp_async_wait0();
         } else {
             for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
                 const uint64_t off = hioff[j >> a.L] | (j & runmask);
