@@ -372,7 +372,9 @@ def test_diagonal_exemption_schedule(dtype, n, g, kinds):
 def test_evc_large_groups(sched):
     """Groups of many strings sharing one x-mask (pure-Z terms, and X/Y masks
     with many Z variants of both nY parities) on 8192-amplitude cosets: the
-    per-group transform path of the EVC pass, per term against the oracle."""
+    per-group transform path (>= 16 strings, with and without X) and the
+    per-string fold path (fewer) of the EVC pass, per term against the
+    oracle."""
     n, g = 17, 3
     rng = np.random.default_rng(4242)
     rows = []
@@ -380,9 +382,9 @@ def test_evc_large_groups(sched):
         r = np.zeros(n, np.uint8)
         r[rng.random(n) < 0.3] = 3
         rows.append(r)
-    for size in (2, 3, 4):                                # three x-masks, 14 Z/Y variants each
+    for size, nvar in ((2, 14), (3, 24), (4, 14)):       # three x-masks with 14 or 24 Z/Y variants
         xs = rng.choice(n - g, size, replace=False)
-        for _ in range(14):
+        for _ in range(nvar):
             r = np.zeros(n, np.uint8)
             r[rng.random(n) < 0.4] = 3
             r[xs] = rng.choice([1, 2], size)
