@@ -15,9 +15,10 @@ order and notation, independent of the library's C++ planner:
   adhoc_schedule            the ad hoc (eager) scheduler of Sec. V-B-1: depth
                             order, and before each wide gate a new mapping
                             chosen for that gate alone (least recently used
-                            local qubits are evicted; the paper gives no
-                            rule, so this one is "parity unpinned" beyond its
-                            definition and invariants)
+                            local qubits are evicted, adhoc_evict_order; the
+                            paper gives no rule, so this reading is pinned
+                            by a trace worked out by hand from it, which
+                            each alternative reading breaks)
   qr_pairs                  physical pairing of one QR (Sec. III-B-4: a
                             subset of Q_L exchanged with an equal-sized
                             subset of Q_G)
@@ -230,6 +231,13 @@ def classify_hierarchical(plan: Plan, n: int) -> list[str]:
     return kinds
 
 
+def adhoc_evict_order(cand: set, last: list[int]) -> list[int]:
+    """Eviction order of the ad hoc rule among candidate local qubits: least
+    recently used first (last[q] = position of the last operation touching
+    q, -1 if none), ties to the highest logical index."""
+    return sorted(cand, key=lambda q: (last[q], -q))
+
+
 def adhoc_schedule(n: int, T: list[tuple], nL: int, l2p=None, order=None) -> Plan:
     """Ad hoc (eager) QR: process in depth order (or the given order); before
     an operation whose targets are not all local, bring its global targets in
@@ -247,7 +255,7 @@ def adhoc_schedule(n: int, T: list[tuple], nL: int, l2p=None, order=None) -> Pla
         tu = set(T[u])
         if not tu <= QL:
             inn = tu - QL
-            cand = sorted(QL - tu, key=lambda q: (last[q], -q))
+            cand = adhoc_evict_order(QL - tu, last)
             evict = set(cand[:len(inn)])
             newQL = (QL - evict) | inn
             pairs, l2p_new = qr_pairs(l2p, QL, newQL)
