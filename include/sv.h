@@ -308,18 +308,21 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch,
  * Expectation values without device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc where they need expectation values (their device memory is
- * owned by another allocator, or an allocation must not synchronise the
- * device at that point).  It computes per_term[t] = <psi|P_t|psi> (host,
- * nullable) and energy = sum_t coeffs[t] per_term[t] (host) for the 2^n
- * amplitudes at state (device, complex64/complex128, taken in index order:
- * bit q of the index is qubit q), using the library's EVC kernels with all
- * scratch in one fixed 1 MiB static device array held by every GPU that
- * loads the library.  At most 256 strings per call; more is EINVAL.  No
- * cudaMalloc/cudaFree is called.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current:
- * make that first call before any stream capture.  All calls share the
- * array; calls whose work overlaps on the GPU race on it.  Synchronises the
- * stream (cudaStream_t as void*, NULL = legacy default stream).
+ * owned by another allocator, or they cannot let an allocation stall every
+ * stream of the device at that point: this call waits for its own stream
+ * only).  It computes per_term[t] = <psi|P_t|psi> (host, nullable) and
+ * energy = sum_t coeffs[t] per_term[t] (host) for the 2^n amplitudes at
+ * state (device, complex64/complex128, 16-byte aligned, else EINVAL before
+ * any launch; taken in index order: bit q of the index is qubit q), using
+ * the library's EVC kernels with all scratch in one fixed 1 MiB static
+ * device array held by every GPU that loads the library.  At most 256
+ * strings per call; more is EINVAL.  No cudaMalloc/cudaFree is called.  The
+ * call runs on the current device, and its first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current.  All calls share the array; calls whose work overlaps on the GPU
+ * race on it.  The call copies its tables from pageable host memory and
+ * synchronises the given stream (cudaStream_t as void*, NULL = legacy
+ * default stream), so it cannot be made inside a stream capture.
  */
 sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, const sv_pauli *paulis,
                             const double *coeffs, size_t nterms, double *energy, double *per_term,

@@ -4,11 +4,13 @@
 // Who needs this: callers that cannot call cudaMalloc at the point where they
 // want expectation values -- for example code whose device memory is owned by
 // another allocator (a framework's caching pool that has already reserved
-// most of HBM, so a raw cudaMalloc fails or fragments it), code that must not
-// let an allocation synchronise the device in the middle of a pipeline, and
-// code that runs inside regions where allocation calls are not permitted.
-// The ordinary entry points (sv_expect and friends) allocate their scratch
-// and plan buffers lazily with cudaMalloc; this one does not.
+// most of HBM, so a raw cudaMalloc fails or fragments it), and code that must
+// not let an allocation stall the whole device (cudaMalloc and cudaFree may
+// wait for work on every stream) in the middle of a pipeline; this call waits
+// only for its own stream.  The ordinary entry points (sv_expect and friends)
+// allocate their scratch and plan buffers lazily with cudaMalloc; this one
+// does not.  It copies its tables from pageable host memory and synchronises
+// its stream, so it cannot be called inside a stream capture.
 //
 // Scratch: one file-scope device array of kNoAllocScratchBytes bytes.  Every
 // GPU that loads this library holds it until the process exits.  All calls
@@ -75,6 +77,10 @@ extern "C" sv_status sv_expect_noalloc(const void *state, int n, sv_dtype dt, co
                                        const double *coeffs, size_t nterms, double *energy, double *per_term,
                                        void *stream) {
     if (!state || !paulis || !coeffs || !energy) return noalloc_fail(SV_EINVAL, "null argument");
+    // the EVC kernels stage the state with 16-byte asynchronous copies: an
+    // unaligned state (e.g. a view at an odd complex64 offset) is refused here,
+    // before anything is launched
+    if ((uintptr_t)state % 16) return noalloc_fail(SV_EINVAL, "state must be 16-byte aligned");
     if (n < 1 || n > sv::kMaxQubits) return noalloc_fail(SV_EINVAL, "n must be in [1, 40]");
     if (dt != SV_C64 && dt != SV_C128) return noalloc_fail(SV_EINVAL, "bad dtype");
     if (nterms < 1 || nterms > (size_t)kNoAllocMaxTerms)

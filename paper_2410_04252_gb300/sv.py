@@ -435,14 +435,18 @@ def expect_noalloc(state, n: int, dtype: int, paulis, coeffs, stream=None, per_t
     """sv_expect_noalloc on a device tensor `state` (index order): returns
     (energy, per-term values).  Allocates no device memory."""
     import torch
+    want = torch.complex64 if dtype == C64 else torch.complex128
+    if not state.is_cuda or state.dtype != want or not state.is_contiguous() or state.numel() != (1 << n):
+        raise ValueError(f"expect_noalloc: state must be a contiguous CUDA {want} tensor of 2^{n} amplitudes")
     coeffs = np.ascontiguousarray(coeffs, np.float64)
     paulis = np.ascontiguousarray(paulis, np.uint64)
-    st = torch.cuda.current_stream(state.device) if stream is None else stream
     e = ctypes.c_double(0.0)
     pt = np.zeros(len(coeffs), np.float64) if per_term else None
-    _check(_lib.sv_expect_noalloc(ctypes.c_void_p(state.data_ptr()), n, dtype, _ptr(paulis), _ptr(coeffs),
-                                  len(coeffs), ctypes.byref(e), _ptr(pt) if pt is not None else None,
-                                  ctypes.c_void_p(st.cuda_stream)))
+    with torch.cuda.device(state.device):     # the C side works on the current device
+        st = torch.cuda.current_stream(state.device) if stream is None else stream
+        _check(_lib.sv_expect_noalloc(ctypes.c_void_p(state.data_ptr()), n, dtype, _ptr(paulis), _ptr(coeffs),
+                                      len(coeffs), ctypes.byref(e), _ptr(pt) if pt is not None else None,
+                                      ctypes.c_void_p(st.cuda_stream)))
     return e.value, pt
 
 

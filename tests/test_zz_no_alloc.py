@@ -1,11 +1,15 @@
 """sv_expect_noalloc (no device allocation; scratch in a static device array)
-against the ordinary sv_expect, through the C ABI, on two calls in a row.
-Collected last so that a failure here leaves every other test already run."""
+against the ordinary sv_expect, through the C ABI, on two calls in a row, and
+against the FP64 oracle from small n (fewer cosets than CTAs) up to the
+256-string limit.  Collected last so that a failure here leaves every other
+test already run."""
+import ctypes
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2410_04252_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -50,3 +54,53 @@ def test_noalloc_rejects_oversize_calls():
     with pytest.raises(sv.SvError) as e:
         sv.expect_noalloc(sim.state, n, sv.C64, paulis, coeffs)
     assert e.value.status == sv.SV_EINVAL and "256" in str(e.value)
+
+
+def _random_state(n, seed, dtype):
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    v /= np.linalg.norm(v)
+    t = torch.tensor(v, dtype=torch.complex64 if dtype == sv.C64 else torch.complex128, device="cuda")
+    # the oracle sees exactly the amplitudes the GPU holds (complex64 rounding included)
+    return t, t.cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("dtype", [sv.C64, sv.C128])
+@pytest.mark.parametrize("n", [1, 3, 6, 9, 14])
+def test_noalloc_matches_oracle(n, dtype):
+    """Per-term values and energy against the oracle's per-string sum; n = 14
+    takes the 256-string maximum (random and Jordan-Wigner-shaped strings)."""
+    state, host = _random_state(n, 500 + n, dtype)
+    hams = [W.random_hamiltonian(n, 256 if n == 14 else 40, 600 + n)]
+    if n >= 2:
+        hams.append(W.jw_hamiltonian(n, 256 if n == 14 else 40, 700 + n))
+    tol_t = 2e-5 if dtype == sv.C64 else 1e-12
+    for h in hams:
+        ref = oracle.expect_terms(host, h)
+        assert np.max(np.abs(ref.imag)) < 1e-12
+        paulis, coeffs = sv.hamiltonian_arrays(h)
+        for _ in range(2):                       # two calls in a row share the array
+            e, pt = sv.expect_noalloc(state, n, dtype, paulis, coeffs)
+            assert np.max(np.abs(pt - ref.real)) < tol_t
+            l1 = float(np.abs(h.coeffs).sum())
+            assert abs(e - float(h.coeffs @ ref.real)) < (1e-4 * l1 if dtype == sv.C64 else 1e-11)
+
+
+def test_noalloc_rejects_unaligned_or_misshapen_state():
+    n = 8
+    state, _ = _random_state(n + 1, 11, sv.C64)
+    h = W.random_hamiltonian(n, 8, 12)
+    paulis, coeffs = sv.hamiltonian_arrays(h)
+    e = ctypes.c_double(0.0)
+    # a complex64 view one element in: 8-byte aligned only; refused before any launch
+    st = sv._lib.sv_expect_noalloc(ctypes.c_void_p(state.data_ptr() + 8), n, sv.C64,
+                                   sv._ptr(paulis), sv._ptr(coeffs), len(coeffs), ctypes.byref(e), None,
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == sv.SV_EINVAL and "aligned" in sv._lib.sv_last_error().decode()
+    with pytest.raises(sv.SvError) as err:                                    # the same through the binding
+        sv.expect_noalloc(state[1:1 + (1 << n)], n, sv.C64, paulis, coeffs)
+    assert err.value.status == sv.SV_EINVAL
+    with pytest.raises(ValueError):
+        sv.expect_noalloc(state, n, sv.C64, paulis, coeffs)                   # 2^(n+1) amplitudes
+    with pytest.raises(ValueError):
+        sv.expect_noalloc(state[: 1 << n], n, sv.C128, paulis, coeffs)        # wrong dtype
