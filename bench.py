@@ -234,15 +234,17 @@ def run_reference(args):
 # ------------------------------------------------------------------- ours --
 
 def reduce_times(dev_ms, wall_ms, steps, world, dist=None, device="cpu"):
-    """Max over ranks of the device and wall times of the timed region, then
-    the per-step time of one rank and the whole-job values (time per step of
-    the job = time / (steps x ranks), every rank running its own replica)."""
+    """Max over ranks of the device and wall times of the timed region.
+    Every rank runs its own replica of the iteration, so one iteration takes
+    the same time at any rank count: returns (device ms, wall ms, device ms
+    per iteration of one replica, whole-job iterations per second = steps x
+    ranks over the device time, wall ms per iteration of one replica)."""
     import torch
     t = torch.tensor([dev_ms, wall_ms], dtype=torch.float64, device=device)
     if dist is not None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dev_ms, wall_ms = float(t[0]), float(t[1])
-    return dev_ms, wall_ms, dev_ms / steps, dev_ms / (steps * world), wall_ms / (steps * world)
+    return dev_ms, wall_ms, dev_ms / steps, steps * world / (dev_ms * 1e-3), wall_ms / steps
 
 
 def run_ours(args):
@@ -340,8 +342,9 @@ def run_ours(args):
     wall_ms = (time.perf_counter() - w0) * 1e3
     barrier()
     clk = clocks.stop()
-    dev_ms, wall_ms, ms_per_step, value, e2e_value = reduce_times(ev0.elapsed_time(ev1), wall_ms, args.steps,
-                                                                   world, dist, "cuda")
+    dev_ms, wall_ms, ms_per_step, job_iters_per_s, e2e_value = reduce_times(ev0.elapsed_time(ev1), wall_ms,
+                                                                             args.steps, world, dist, "cuda")
+    value = ms_per_step
 
     # eager schedule on the same GPU (shorter run)
     eager = None
@@ -465,6 +468,8 @@ def run_ours(args):
                                    "in, energy out)",
                         "qsu": "wall clock around reset + apply_circuit + synchronize (host params in)"}[work]},
         "gpu_launches": launches,
+        "replicas": {"n": world, "iterations_per_s": job_iters_per_s,
+                     "how": "every rank runs its own replica; value is one replica's time per iteration"},
         "clocks": clk,
         "kernels": kinds,
         "counts": counts,

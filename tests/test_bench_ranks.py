@@ -1,6 +1,7 @@
 """The multi-rank timing path of bench.py on CPU: two gloo ranks (one process
 each, as torchrun starts them) reduce their timed-region lengths to the max
-over ranks, and the whole-job value counts every rank's replica."""
+over ranks; the reported time per iteration is one replica's, and the
+whole-job throughput counts every rank's replica."""
 import multiprocessing as mp
 import os
 import socket
@@ -40,13 +41,15 @@ def test_reduce_times_two_gloo_ranks():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, dev, wall, per_step, value, e2e in got:
+    for rank, dev, wall, per_step, iters_per_s, e2e in got:
         assert dev == 200.0 and wall == 151.0          # max over the ranks, the same on every rank
-        assert per_step == 50.0                         # one rank's time per step
-        assert value == 25.0                            # 2 replicas x 4 steps in 200 ms
-        assert e2e == pytest.approx(151.0 / 8)
+        assert per_step == 50.0                         # one replica's time per iteration
+        assert iters_per_s == pytest.approx(40.0)       # 2 replicas x 4 iterations in 200 ms
+        assert e2e == pytest.approx(151.0 / 4)          # one replica's wall time per iteration
 
 
 def test_reduce_times_single_rank():
     import bench
-    assert bench.reduce_times(90.0, 120.0, 3, 1) == (90.0, 120.0, 30.0, 30.0, 40.0)
+    dev, wall, per_step, iters_per_s, e2e = bench.reduce_times(90.0, 120.0, 3, 1)
+    assert (dev, wall, per_step, e2e) == (90.0, 120.0, 30.0, 40.0)
+    assert iters_per_s == pytest.approx(3 / 0.09)
