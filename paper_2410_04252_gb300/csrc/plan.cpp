@@ -306,6 +306,78 @@ std::string adhoc_schedule(int n, int nL, const std::vector<Op> &ops, const std:
 // the earliest remaining gates), padded with the lowest free local bits; the
 // pass then takes gates like Alg. 2 (a gate that does not fit blocks its
 // targets), which keeps the dependency order C1.
+// Gates a pass staging S would take (the Alg. 2 scan: a gate that does not
+// fit blocks its targets), at most cap.
+int pass_take_count(const std::vector<int32_t> &remain, const std::vector<uint64_t> &pm, uint64_t S, int cap) {
+    uint64_t av = S;
+    int c = 0;
+    for (int32_t u : remain) {
+        const uint64_t t = pm[u];
+        if ((t & ~av) == 0) {
+            if (++c >= cap) break;
+        } else {
+            av &= ~t;
+        }
+        if (!av) break;
+    }
+    return c;
+}
+
+// Staged set of the next pass.  Two candidates: (a) the targets of the
+// earliest remaining gates (Alg. 3 style), padded with the lowest free local
+// bits; (b) grown from the low bits step by step, each step adding either one
+// local bit or all missing targets of one of the earliest remaining gates,
+// whichever lets the pass take the most gates per added bit (ties: fewer
+// bits, then the earlier candidate).  (b) follows the light cone of a circuit
+// instead of its earliest layer.  The candidate taking more gates wins, (a)
+// on a tie.
+uint64_t choose_staged(const std::vector<int32_t> &remain, const std::vector<uint64_t> &pm, uint64_t lowmask,
+                       uint64_t localbits, int k, int cap) {
+    uint64_t Sa = lowmask, avail = localbits;
+    for (int32_t u : remain) {
+        uint64_t t = pm[u];
+        if ((t & ~avail) == 0 && popc(Sa | t) <= k) Sa |= t;
+        else avail &= ~t;
+        if (!avail || popc(Sa) == k) break;
+    }
+    for (uint64_t fr = localbits & ~Sa; popc(Sa) < k && fr; fr &= fr - 1) Sa |= bit(lobit(fr));
+    // candidate bits in order of first appearance among the remaining targets
+    std::vector<int> cand;
+    uint64_t seen = lowmask;
+    for (int32_t u : remain) {
+        for (uint64_t t = pm[u] & localbits & ~seen; t; t &= t - 1) cand.push_back(lobit(t));
+        seen |= pm[u] & localbits;
+        if ((seen & localbits) == localbits) break;
+    }
+    uint64_t Sb = lowmask;
+    const int base_c = pass_take_count(remain, pm, Sb, cap);
+    int cur_c = base_c;
+    while (popc(Sb) < k) {
+        std::vector<uint64_t> adds;
+        for (int b : cand)
+            if (!(Sb >> b & 1)) adds.push_back(bit(b));
+        int looked = 0;
+        for (int32_t u : remain) {
+            const uint64_t miss = pm[u] & localbits & ~Sb;
+            if (popc(miss) > 1 && popc(Sb | miss) <= k) adds.push_back(miss);
+            if (++looked >= 64) break;
+        }
+        uint64_t best = 0;
+        double bestr = -1.0;
+        int bestn = 0;
+        for (uint64_t a : adds) {
+            const int na = popc(a);
+            const double r = (double)(pass_take_count(remain, pm, Sb | a, cap) - cur_c) / na;
+            if (r > bestr || (r == bestr && na < bestn)) { bestr = r; best = a; bestn = na; }
+        }
+        if (!best) break;
+        Sb |= best;
+        cur_c = pass_take_count(remain, pm, Sb, cap);
+    }
+    for (uint64_t fr = localbits & ~Sb; popc(Sb) < k && fr; fr &= fr - 1) Sb |= bit(lobit(fr));
+    return pass_take_count(remain, pm, Sb, cap) > pass_take_count(remain, pm, Sa, cap) ? Sb : Sa;
+}
+
 void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, int fuse_max, bool dx) {
     const int nL = P.nL;
     const int cap = (fuse_max > 0 && fuse_max < kMaxPassOps) ? fuse_max : kMaxPassOps;
@@ -321,14 +393,7 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, in
         for (int32_t u : remain) pm[u] = to_physical(ops[u].tmask, T.l2p) & (dx ? localbits : ~0ull);
         std::vector<int32_t> G, next;
         while (!remain.empty()) {
-            uint64_t S = lowmask, avail = localbits;
-            for (int32_t u : remain) {
-                uint64_t t = pm[u];
-                if ((t & ~avail) == 0 && popc(S | t) <= k) S |= t;
-                else avail &= ~t;
-                if (!avail || popc(S) == k) break;
-            }
-            for (uint64_t fr = localbits & ~S; popc(S) < k && fr; fr &= fr - 1) S |= bit(lobit(fr));
+            const uint64_t S = choose_staged(remain, pm, lowmask, localbits, k, cap);
             uint64_t av = S;
             G.clear();
             for (int32_t u : remain) {
