@@ -90,6 +90,9 @@ GatePassArgs gate_args(int n, const GatePass &gp) {
     a.ph_end = gp.ph_end;
     a.db_begin = gp.db_begin;
     a.db_end = gp.db_end;
+    a.st_begin = gp.st_begin;
+    a.st_end = gp.st_end;
+    a.area = gp.area;
     return a;
 }
 
@@ -119,12 +122,12 @@ struct QsuEntry {
     uint64_t key = 0;
     QsuPlan plan;
     std::vector<GatePassArgs> args;
-    DevBuf ops, gparam, csr_off, csr_idx, phases, dblocks, dmembers;
+    DevBuf ops, gparam, csr_off, csr_idx, phases, steps, dblocks, dmembers;
     int m = 0, np = 0;
     double plan_ms = 0;
     uint64_t last_use = 0;
     void release() {
-        ops.release(); gparam.release(); csr_off.release(); csr_idx.release(); phases.release();
+        ops.release(); gparam.release(); csr_off.release(); csr_idx.release(); phases.release(); steps.release();
         dblocks.release(); dmembers.release();
     }
 };
@@ -383,7 +386,7 @@ sv_status get_qsu(sv_handle *h, const sv_gate *gates, size_t m, size_t np, sv_sc
     PlanOptions po = plan_options(h->opt);
     if (sched == SV_SCHED_HIER) po.hier_intra = h->opt.intra_bits;
     po.diag_exempt = sched == SV_SCHED_LAZY_DIAG;
-    po.max_diag = h->dt == SV_C64 ? kMaxPassDiag : 3;     // complex128 tables are twice as large
+    po.amp_bytes = h->dt == SV_C64 ? 8 : 16;              // the diagonal blocks' shared-memory budget
     std::string err = plan_qsu(h->n, sched == SV_SCHED_DIRECT ? 0 : h->g, gates, m, sched != SV_SCHED_EAGER, po,
                                h->l2p, ent->plan);
     if (!err.empty()) return fail(SV_EINVAL, "QSU plan: " + err);
@@ -394,6 +397,7 @@ sv_status get_qsu(sv_handle *h, const sv_gate *gates, size_t m, size_t np, sv_sc
     for (auto &gp : ent->plan.passes) ent->args.push_back(gate_args(h->n, gp));
     SV_CK(upload(ent->ops, ent->plan.ops, h->stream));
     SV_CK(upload(ent->phases, ent->plan.phases, h->stream));
+    SV_CK(upload(ent->steps, ent->plan.steps, h->stream));
     SV_CK(upload(ent->dblocks, ent->plan.dblocks, h->stream));
     SV_CK(upload(ent->dmembers, ent->plan.dmembers, h->stream));
     std::vector<int32_t> gparam(m);
@@ -588,7 +592,7 @@ sv_status run_forward(sv_handle *h, QsuEntry *q, sv_stats *st) {
                 Rec r(h, st, SV_K_GATE, 2.0 * (double)h->state_bytes());
                 const int rg = (int)std::min<uint64_t>(ntiles, (uint64_t)device_sms());
                 SV_CK(launch_gate_reg(h->dt, h->stream, rg, h->psi, a, q->ops.as<DevOp>(), q->phases.as<Phase>(),
-                                      h->coef.p, h->mats.p, q->dblocks.as<DiagBlock>(),
+                                      q->steps.as<RegStep>(), h->coef.p, h->mats.p, q->dblocks.as<DiagBlock>(),
                                       q->dmembers.as<DiagMember>()));
             } else {
                 Rec r(h, st, SV_K_GATE, 2.0 * (double)h->state_bytes());
@@ -708,8 +712,9 @@ sv_status run_reverse(sv_handle *h, QsuEntry *q, sv_stats *st) {
             Rec r(h, st, SV_K_ADJ, 4.0 * (double)h->state_bytes());
             if (a.ph_begin >= 0)
                 SV_CK(launch_adj_reg(h->dt, h->stream, grid, h->psi, h->lam, a, q->ops.as<DevOp>(),
-                                     q->phases.as<Phase>(), h->coef.p, h->mats.p, h->part.as<double>(), nops,
-                                     q->dblocks.as<DiagBlock>(), q->dmembers.as<DiagMember>()));
+                                     q->phases.as<Phase>(), q->steps.as<RegStep>(), h->coef.p, h->mats.p,
+                                     h->part.as<double>(), nops, q->dblocks.as<DiagBlock>(),
+                                     q->dmembers.as<DiagMember>()));
             else
                 SV_CK(launch_adj_pass(h->dt, h->stream, grid, threads, h->psi, h->lam, a, q->ops.as<DevOp>(),
                                       h->coef.p, h->mats.p, h->part.as<double>(), nops));

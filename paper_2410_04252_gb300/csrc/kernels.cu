@@ -833,94 +833,254 @@ __device__ __forceinline__ void phase_index(uint32_t rmask, int k, uint32_t &bas
     for (int v = 1; v < (1 << RB); ++v) sp[v] = sp[v & (v - 1)] | rb[__ffs(v) - 1];
 }
 
-// Gate data of a pass staged in shared memory once per CTA: kind, targets and
-// (cos, sin) of the half angle, so that a gate costs one shared load.
+// ---- register-blocked pass execution ----------------------------------
+// Complex64 amplitudes stay in one 64-bit register pair (re, im) while a
+// phase is in registers, so that rotations with real coefficients are pure
+// packed f32x2 arithmetic; complex128 ones are double2.
+template <typename R> struct RegT;
+template <> struct RegT<float> { using T = unsigned long long; };
+template <> struct RegT<double> { using T = double2; };
+template <typename R> using RA = typename RegT<R>::T;
+
+template <typename R> __device__ __forceinline__ Cx<R> ra_cx(RA<R> a);
+template <> __device__ __forceinline__ float2 ra_cx<float>(unsigned long long a) { return f2_unpack(a); }
+template <> __device__ __forceinline__ double2 ra_cx<double>(double2 a) { return a; }
+template <typename R> __device__ __forceinline__ RA<R> cx_ra(Cx<R> a);
+template <> __device__ __forceinline__ unsigned long long cx_ra<float>(float2 a) { return f2_pack(a.x, a.y); }
+template <> __device__ __forceinline__ double2 cx_ra<double>(double2 a) { return a; }
+
+template <typename R> __device__ __forceinline__ RA<R> ra_neg(RA<R> a);
+template <> __device__ __forceinline__ unsigned long long ra_neg<float>(unsigned long long a) {
+    return a ^ 0x8000000080000000ull;
+}
+template <> __device__ __forceinline__ double2 ra_neg<double>(double2 a) { return make_double2(-a.x, -a.y); }
+
+// a * w (complex), or a * conj(w)
 template <typename R>
-struct StagedOp {
-    R c, s;
-    int32_t ry;    // 1 + register bit of an RY whose target is a register bit of its phase, else 0
-    int32_t pad;
-    DevOp op;
-};
-
-// Stages ops [begin, end) of a pass; phases [ph_begin, ph_end) give each op's
-// register set (rmask), so that the common RY case dispatches on one staged
-// field.
-template <typename R>
-__device__ __forceinline__ void stage_ops(StagedOp<R> *so, const DevOp *ops, int begin, int end, const R *coef,
-                                          const Phase *phases, int ph_begin, int ph_end) {
-    for (int o = begin + threadIdx.x; o < end; o += blockDim.x) {
-        StagedOp<R> x;
-        x.op = ops[o];
-        x.c = coef[2 * x.op.gate];
-        x.s = coef[2 * x.op.gate + 1];
-        x.ry = 0;
-        x.pad = 0;
-        if (x.op.kind == SV_RY && x.op.t[0] >= 0 && x.op.t[0] < 32) {
-            for (int ph = ph_begin; ph < ph_end; ++ph) {
-                const Phase P = phases[ph];
-                if (o < P.op_begin || o >= P.op_end) continue;
-                const int t0 = x.op.t[0];
-                if ((P.rmask >> t0) & 1u) x.ry = 1 + __popc(P.rmask & ((1u << t0) - 1u));
-                break;
-            }
-        }
-        so[o - begin] = x;
-    }
+__device__ __forceinline__ RA<R> ra_cmul(RA<R> a, Cx<R> w) {
+    const Cx<R> x = ra_cx<R>(a);
+    return cx_ra<R>(mk<R>(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x));
 }
 
-// ---- diagonal blocks (see DiagBlock): per launch, every thread builds its
-// thread factor C and CZ sign pattern M for each block of the pass, and the
-// first 2^RB threads the register table Rt; adj builds the tables of D^dagger.
-__device__ __forceinline__ uint32_t reg_bit_pattern(int a) {   // v in [0, 16) with bit a set
-    return a == 0 ? 0xAAAAu : a == 1 ? 0xCCCCu : a == 2 ? 0xF0F0u : 0xFF00u;
+// One RY's coefficients, packed once per gate.
+template <typename R> struct RotK;
+template <> struct RotK<float> { unsigned long long C, S, NS; };
+template <> struct RotK<double> { double c, s; };
+template <typename R> __device__ __forceinline__ RotK<R> rotk(R c, R s);
+template <> __device__ __forceinline__ RotK<float> rotk<float>(float c, float s) {
+    return {f2_pack(c, c), f2_pack(s, s), f2_pack(-s, -s)};
 }
+template <> __device__ __forceinline__ RotK<double> rotk<double>(double c, double s) { return {c, s}; }
 
-template <typename R, int RB>
-__device__ void diag_setup(const GatePassArgs &a, const DiagBlock *__restrict__ blocks,
-                           const DiagMember *__restrict__ mem, const StagedOp<R> *so, Cx<R> *Rt, Cx<R> *C,
-                           uint16_t *M, bool adj) {
-    constexpr int V = 1 << RB;
-    const int NT = blockDim.x;
-    for (int lb = 0; lb < a.db_end - a.db_begin; ++lb) {
-        const DiagBlock B = blocks[a.db_begin + lb];
-        uint32_t base, sp[V];
-        phase_index<RB>(B.rmask, a.k, base, sp);
-        Cx<R> w = mk<R>(1, 0);
-        uint32_t msk = 0;
-        const int v = threadIdx.x;
-        Cx<R> r = mk<R>(1, 0);
-        for (int mi = B.m_begin; mi < B.m_end; ++mi) {
-            const DiagMember m = mem[mi];
-            const StagedOp<R> o = so[m.op - a.op_begin];
-            const R sgn = adj ? -o.s : o.s;
-            switch (m.type) {
-            case SV_DM_THR_RZ: w = cmul<R>(w, mk<R>(o.c, ((base >> m.a) & 1u) ? sgn : -sgn)); break;
-            case SV_DM_THR_CZ: if ((base >> m.a) & (base >> m.b) & 1u) w = mk<R>(-w.x, -w.y); break;
-            case SV_DM_MIX_CZ: if ((base >> m.b) & 1u) msk ^= reg_bit_pattern(m.a); break;
-            case SV_DM_REG_RZ: r = cmul<R>(r, mk<R>(o.c, ((v >> m.a) & 1) ? sgn : -sgn)); break;
-            case SV_DM_REG_CZ: if ((v >> m.a) & (v >> m.b) & 1) r = mk<R>(-r.x, -r.y); break;
-            default: break;
-            }
-        }
-        C[lb * NT + threadIdx.x] = w;
-        M[lb * NT + threadIdx.x] = (uint16_t)msk;
-        if (threadIdx.x < V) Rt[lb * 16 + threadIdx.x] = r;
-    }
-}
-
-// x[v] *= C * Rt[v] * (-1)^{M_v}
-template <typename R, int RB>
-__device__ __forceinline__ void diag_apply(Cx<R> *x, int lb, const Cx<R> *Rt, const Cx<R> *C, const uint16_t *M) {
-    constexpr int V = 1 << RB;
-    const Cx<R> c = C[lb * blockDim.x + threadIdx.x];
-    const uint32_t msk = M[lb * blockDim.x + threadIdx.x];
+// (u, v) <- (c u - s v, s u + c v) on every pair of register bit B
+template <typename R, int V, int B>
+__device__ __forceinline__ void ra_rot(RA<R> *x, const RotK<R> &k) {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        Cx<R> w = cmul<R>(c, Rt[lb * 16 + v]);
-        if ((msk >> v) & 1u) w = mk<R>(-w.x, -w.y);
-        x[v] = cmul<R>(x[v], w);
+        if (v & (1 << B)) continue;
+        const int w = v | (1 << B);
+        if constexpr (sizeof(R) == 4) {
+            unsigned long long t, uu, vv;
+            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(x[w]), "l"(k.NS));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(x[v]), "l"(k.C), "l"(t));
+            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(x[w]), "l"(k.C));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(x[v]), "l"(k.S), "l"(t));
+            x[v] = uu;
+            x[w] = vv;
+        } else {
+            const double2 a = x[v], b = x[w];
+            x[v] = make_double2(k.c * a.x - k.s * b.x, k.c * a.y - k.s * b.y);
+            x[w] = make_double2(k.s * a.x + k.c * b.x, k.s * a.y + k.c * b.y);
+        }
     }
+}
+
+// Gradient part of an RY on register bit B: sum over pairs (v, w = v | bit B)
+// of Re(conj(l_w) p_v) - Re(conj(l_v) p_w)  (= Im<lambda|Y|psi> on the pairs).
+template <typename R, int V, int B>
+__device__ __forceinline__ R ra_ry_grad(const RA<R> *p, const RA<R> *l) {
+    if constexpr (sizeof(R) == 4) {
+        unsigned long long P = 0, M = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (v & (1 << B)) continue;
+            const int w = v | (1 << B);
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(P) : "l"(l[w]), "l"(p[v]), "l"(P));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(M) : "l"(l[v]), "l"(p[w]), "l"(M));
+        }
+        const float2 a = f2_unpack(P), b = f2_unpack(M);
+        return (a.x + a.y) - (b.x + b.y);
+    } else {
+        double g = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (v & (1 << B)) continue;
+            const int w = v | (1 << B);
+            g += (l[w].x * p[v].x + l[w].y * p[v].y) - (l[v].x * p[w].x + l[v].y * p[w].y);
+        }
+        return g;
+    }
+}
+
+// Four values reduced over a warp at once: lane L ends with the warp total
+// of value L >> 3 (6 shuffles instead of 20).
+template <typename R>
+__device__ __forceinline__ R warp_sum4(R v0, R v1, R v2, R v3) {
+    const unsigned lane = threadIdx.x & 31u;
+    const bool hi = lane & 16u;
+    R k0 = hi ? v2 : v0, k1 = hi ? v3 : v1;
+    k0 += __shfl_xor_sync(0xffffffffu, hi ? v0 : v2, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, hi ? v1 : v3, 16);
+    const bool h8 = lane & 8u;
+    R k = (h8 ? k1 : k0) + __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+template <typename R, int V, int B>
+__device__ __forceinline__ void ra_mat1(RA<R> *x, const Cx<R> *M, bool adj) {
+    const Cx<R> m00 = mel<R>(M, 2, 0, 0, adj), m01 = mel<R>(M, 2, 0, 1, adj);
+    const Cx<R> m10 = mel<R>(M, 2, 1, 0, adj), m11 = mel<R>(M, 2, 1, 1, adj);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if (v & (1 << B)) continue;
+        const int w = v | (1 << B);
+        const Cx<R> a = ra_cx<R>(x[v]), b = ra_cx<R>(x[w]);
+        x[v] = cx_ra<R>(mk<R>(m00.x * a.x - m00.y * a.y + m01.x * b.x - m01.y * b.y,
+                              m00.x * a.y + m00.y * a.x + m01.x * b.y + m01.y * b.x));
+        x[w] = cx_ra<R>(mk<R>(m10.x * a.x - m10.y * a.y + m11.x * b.x - m11.y * b.y,
+                              m10.x * a.y + m10.y * a.x + m11.x * b.y + m11.y * b.x));
+    }
+}
+
+#define SV_RB_SWITCH(b, CALL)                                    \
+    switch (b) {                                                 \
+    case 0: CALL(0); break;                                      \
+    case 1: if constexpr (RB > 1) { CALL(1); } break;            \
+    case 2: if constexpr (RB > 2) { CALL(2); } break;            \
+    case 3: if constexpr (RB > 3) { CALL(3); } break;            \
+    default: break;                                              \
+    }
+
+// One operation applied by the generic path (OP steps) on register
+// amplitudes: base = the thread's tile bits outside rmask; cs = (cos, sin)
+// of the half angle (sin already negated for an inverse).
+template <typename R, int RB>
+__device__ void ra_apply_op(RA<R> *x, DevOp op, uint32_t rmask, uint32_t base, Cx<R> cs, const Cx<R> *mats,
+                            bool adj) {
+    constexpr int V = 1 << RB;
+    const int t0 = op.t[0];
+    const int b0 = __popc(rmask & ((1u << (t0 & 31)) - 1u));
+    switch (op.kind) {
+    case SV_RY: {
+        const RotK<R> k = rotk<R>(cs.x, cs.y);
+#define SV_C(B) ra_rot<R, V, B>(x, k)
+        SV_RB_SWITCH(b0, SV_C)
+#undef SV_C
+        break;
+    }
+    case SV_MAT1: {
+        const Cx<R> *M = mats + op.mat;
+#define SV_C(B) ra_mat1<R, V, B>(x, M, adj)
+        SV_RB_SWITCH(b0, SV_C)
+#undef SV_C
+        break;
+    }
+    case SV_RZ: {
+        if ((rmask >> t0) & 1u) {
+            const Cx<R> w0 = mk<R>(cs.x, -cs.y), w1 = mk<R>(cs.x, cs.y);
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = ra_cmul<R>(x[v], ((v >> b0) & 1) ? w1 : w0);
+        } else {
+            const Cx<R> w = mk<R>(cs.x, ((base >> t0) & 1u) ? cs.y : -cs.y);
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[v] = ra_cmul<R>(x[v], w);
+        }
+        break;
+    }
+    case SV_CZ: {
+        const int t1 = op.t[1];
+        const bool r0 = (rmask >> t0) & 1u, r1 = (rmask >> t1) & 1u;
+        uint32_t negmask = 0;   // register amplitudes that change sign
+        if (r0 && r1) {
+            const int b1 = __popc(rmask & ((1u << t1) - 1u));
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if ((v >> b0) & (v >> b1) & 1) negmask |= 1u << v;
+        } else if (r0 || r1) {
+            const int tr = r0 ? t0 : t1, tt = r0 ? t1 : t0;
+            if ((base >> tt) & 1u) {
+                const int br = __popc(rmask & ((1u << tr) - 1u));
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if ((v >> br) & 1) negmask |= 1u << v;
+            }
+        } else if (((base >> t0) & (base >> t1)) & 1u) {
+            negmask = 0xFFFFFFFFu;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if ((negmask >> v) & 1u) x[v] = ra_neg<R>(x[v]);
+        break;
+    }
+    case SV_OP_PHASE: {
+        const Cx<R> w = mk<R>(cs.x, op.t[0] ? cs.y : -cs.y);
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = ra_cmul<R>(x[v], w);
+        break;
+    }
+    case SV_OP_ZSIGN: {
+        const bool reg = (rmask >> t0) & 1u;
+        const bool thr = !reg && ((base >> t0) & 1u);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+            if (reg ? ((v >> b0) & 1) : thr) x[v] = ra_neg<R>(x[v]);
+        break;
+    }
+    case SV_OP_NEG: {
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = ra_neg<R>(x[v]);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
+// Im(conj(l) p) per register amplitude
+template <typename R>
+__device__ __forceinline__ R ra_imdot(RA<R> l, RA<R> p) {
+    const Cx<R> a = ra_cx<R>(l), b = ra_cx<R>(p);
+    return a.x * b.y - a.y * b.x;
+}
+
+// Adjoint of one OP step: gradient part Im<lambda|G|psi> (RY: Y, RZ: Z), then
+// U^dagger on both register sets.  cs holds (cos, -sin).
+template <typename R, int RB>
+__device__ R ra_adjoint_op(RA<R> *p, RA<R> *l, DevOp op, uint32_t rmask, uint32_t base, Cx<R> cs,
+                           const Cx<R> *mats) {
+    constexpr int V = 1 << RB;
+    const int t0 = op.t[0];
+    const int b0 = __popc(rmask & ((1u << (t0 & 31)) - 1u));
+    R g = 0;
+    if (op.kind == SV_RY) {
+#define SV_C(B) g = ra_ry_grad<R, V, B>(p, l)
+        SV_RB_SWITCH(b0, SV_C)
+#undef SV_C
+    } else if (op.kind == SV_RZ || op.kind == SV_OP_PHASE) {
+        const bool reg = op.kind == SV_RZ && ((rmask >> t0) & 1u);
+        const bool one = op.kind == SV_OP_PHASE ? op.t[0] != 0 : ((base >> t0) & 1u) != 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const R im = ra_imdot<R>(l[v], p[v]);
+            g += (reg ? ((v >> b0) & 1) : one) ? -im : im;
+        }
+    }
+    ra_apply_op<R, RB>(p, op, rmask, base, cs, mats, true);
+    ra_apply_op<R, RB>(l, op, rmask, base, cs, mats, true);
+    return g;
 }
 
 // Hint: bring [p, p + bytes) into L2 (bytes a multiple of 16, p 16-byte aligned).
@@ -930,7 +1090,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 
 // One amplitude (8 or 16 bytes) copied global -> shared asynchronously.
 template <typename R>
-__device__ __forceinline__ void cp_async_amp(Cx<R> *dst, const Cx<R> *src) {
+__device__ __forceinline__ void cp_async_amp(void *dst, const Cx<R> *src) {
     if (sizeof(Cx<R>) == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
     else
@@ -938,36 +1098,171 @@ __device__ __forceinline__ void cp_async_amp(Cx<R> *dst, const Cx<R> *src) {
 }
 
 // Issue the copies of one gate-pass tile (swizzled layout) into shared memory.
-template <typename R>
-__device__ __forceinline__ void load_tile_async(Cx<R> *tile, const Cx<R> *psi, uint64_t gbase,
+template <typename R, typename E>
+__device__ __forceinline__ void load_tile_async(E *tile, const Cx<R> *psi, uint64_t gbase,
                                                 const uint64_t *hioff, int nlow, uint32_t T) {
     const uint32_t lowmask = (1u << nlow) - 1u;
     for (uint32_t j = threadIdx.x; j < T; j += blockDim.x)
         cp_async_amp<R>(&tile[swz_tile(j)], &psi[gbase | hioff[j >> nlow] | (j & lowmask)]);
 }
 
+// Shared-memory layout of a register-blocked pass (both kernels): the tiles,
+// then these tables (offsets in bytes from the end of the tiles).
+struct RegLayout {
+    uint32_t hioff, cs, steps, blocks, pbase, prb, acc, area, total;
+};
+__host__ __device__ inline uint32_t align16u(uint32_t v) { return (v + 15u) & ~15u; }
+__host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, bool adj) {
+    RegLayout L;
+    const uint32_t nops = (uint32_t)(a.op_end - a.op_begin), nst = (uint32_t)(a.st_end - a.st_begin);
+    const uint32_t nph = (uint32_t)(a.ph_end - a.ph_begin), nb = (uint32_t)(a.db_end - a.db_begin);
+    uint32_t o = 0;
+    L.hioff = o; o = align16u(o + 8u * (1u << (a.k - a.nlow)));
+    L.cs = o;    o = align16u(o + (uint32_t)amp * nops);
+    L.steps = o; o = align16u(o + 16u * nst);
+    L.blocks = o; o = align16u(o + (uint32_t)sizeof(DiagBlock) * nb);
+    L.pbase = o; o = align16u(o + 2u * kRegThreads * nph);
+    L.prb = o;   o = align16u(o + 8u * nph);
+    L.acc = o;   o = align16u(o + (adj ? 8u * (kRegThreads / 32) * nops : 0u));
+    L.area = o;  o = align16u(o + (uint32_t)a.area);
+    L.total = o;
+    return L;
+}
+
+// Per-launch set-up shared by both kernels: high offsets, (cos, sin) per op
+// (sin negated for the adjoint), steps, blocks, each phase's thread base and
+// swizzled register-bit offsets, and the diagonal blocks' data (of D, or of
+// D^dagger for the adjoint): a register block's table T[v][zm] and every
+// thread's zm, a thread block's factor per thread.
+template <typename R, int RB>
+__device__ void reg_setup(unsigned char *sm, const RegLayout &L, const GatePassArgs &a, const DevOp *ops,
+                          const Phase *phases, const RegStep *steps, const R *coef, const DiagBlock *dblocks,
+                          const DiagMember *dmem, bool adj) {
+    constexpr int V = 1 << RB;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    uint64_t *hioff = reinterpret_cast<uint64_t *>(sm + L.hioff);
+    Cx<R> *cs = reinterpret_cast<Cx<R> *>(sm + L.cs);
+    RegStep *st = reinterpret_cast<RegStep *>(sm + L.steps);
+    DiagBlock *bl = reinterpret_cast<DiagBlock *>(sm + L.blocks);
+    uint16_t *pbase = reinterpret_cast<uint16_t *>(sm + L.pbase);
+    uint16_t *prb = reinterpret_cast<uint16_t *>(sm + L.prb);
+    const uint32_t nh = 1u << (a.k - a.nlow);
+    for (uint32_t j = tid; j < nh; j += NT) hioff[j] = deposit(j, a.hi, a.nhi);
+    for (int o = a.op_begin + tid; o < a.op_end; o += NT) {
+        const int gi = ops[o].gate;
+        cs[o - a.op_begin] = mk<R>(coef[2 * gi], adj ? -coef[2 * gi + 1] : coef[2 * gi + 1]);
+    }
+    for (int s = a.st_begin + tid; s < a.st_end; s += NT) st[s - a.st_begin] = steps[s];
+    for (int b = a.db_begin + tid; b < a.db_end; b += NT) bl[b - a.db_begin] = dblocks[b];
+    for (int ph = a.ph_begin; ph < a.ph_end; ++ph) {
+        const uint32_t rmask = phases[ph].rmask;
+        uint32_t base, sp[V];
+        phase_index<RB>(rmask, a.k, base, sp);
+        pbase[(ph - a.ph_begin) * NT + tid] = (uint16_t)base;
+        if (tid < 4) {
+            uint32_t rm = rmask, bitv = 0;
+            for (int i = 0; i <= tid && rm; ++i) {
+                bitv = rm & (0u - rm);
+                rm ^= bitv;
+            }
+            prb[(ph - a.ph_begin) * 4 + tid] = (uint16_t)(tid < RB ? swz_tile(bitv) : 0u);
+        }
+    }
+    unsigned char *area = sm + L.area;
+    for (int b = a.db_begin; b < a.db_end; ++b) {
+        const DiagBlock B = dblocks[b];
+        uint32_t base, sp[V];
+        phase_index<RB>(B.rmask, a.k, base, sp);
+        if (B.kind == 0) {
+            Cx<R> *tab = reinterpret_cast<Cx<R> *>(area + B.smem);
+            uint8_t *zmv = area + B.smem + V * V * (int)sizeof(Cx<R>);
+            if (tid < V * V) {
+                const int v = tid / V, zm = tid % V;
+                Cx<R> r = mk<R>(((__popc((uint32_t)(v & zm)) & 1) ? -1 : 1), 0);
+                for (int mi = B.m_begin; mi < B.m_end; ++mi) {
+                    const DiagMember m = dmem[mi];
+                    if (m.type == SV_DM_REG_RZ) {
+                        const int gi = ops[m.op].gate;
+                        const R c = coef[2 * gi], s = adj ? -coef[2 * gi + 1] : coef[2 * gi + 1];
+                        r = cmul<R>(r, mk<R>(c, ((v >> m.a) & 1) ? s : -s));
+                    } else if (m.type == SV_DM_REG_CZ) {
+                        if ((v >> m.a) & (v >> m.b) & 1) r = mk<R>(-r.x, -r.y);
+                    }
+                }
+                tab[v * V + zm] = r;
+            }
+            uint32_t zm = 0;
+            for (int mi = B.m_begin; mi < B.m_end; ++mi) {
+                const DiagMember m = dmem[mi];
+                if (m.type == SV_DM_MIX_CZ && ((base >> m.b) & 1u)) zm ^= 1u << m.a;
+            }
+            zmv[tid] = (uint8_t)zm;
+        } else {
+            Cx<R> w = mk<R>(1, 0);
+            for (int mi = B.m_begin; mi < B.m_end; ++mi) {
+                const DiagMember m = dmem[mi];
+                if (m.type == SV_DM_THR_RZ) {
+                    const int gi = ops[m.op].gate;
+                    const R c = coef[2 * gi], s = adj ? -coef[2 * gi + 1] : coef[2 * gi + 1];
+                    w = cmul<R>(w, mk<R>(c, ((base >> m.a) & 1u) ? s : -s));
+                } else if (m.type == SV_DM_THR_CZ) {
+                    if ((base >> m.a) & (base >> m.b) & 1u) w = mk<R>(-w.x, -w.y);
+                }
+            }
+            reinterpret_cast<Cx<R> *>(area + B.smem)[tid] = w;
+        }
+    }
+}
+
+// x[v] *= the block's factor (register block: table entry [v][zm]; thread block: one factor)
+template <typename R, int RB>
+__device__ __forceinline__ void reg_diag(RA<R> *x, const DiagBlock &B, const unsigned char *area) {
+    constexpr int V = 1 << RB;
+    if (B.kind == 0) {
+        const Cx<R> *tab = reinterpret_cast<const Cx<R> *>(area + B.smem);
+        const uint32_t zm = area[B.smem + V * V * (int)sizeof(Cx<R>) + threadIdx.x];
+        const Cx<R> *col = tab + zm;
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = ra_cmul<R>(x[v], col[v * V]);
+    } else {
+        const Cx<R> w = reinterpret_cast<const Cx<R> *>(area + B.smem)[threadIdx.x];
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[v] = ra_cmul<R>(x[v], w);
+    }
+}
+
+// The thread's 2^RB shared-memory indices of a phase (swizzled; the swizzle
+// is linear, so index(base | sp[v]) = swz(base) ^ XOR of swz(register bits)).
+template <int RB>
+__device__ __forceinline__ void phase_slots(uint32_t *idx, uint32_t base, const uint16_t *prb) {
+    idx[0] = swz_tile(base);
+#pragma unroll
+    for (int v = 1; v < (1 << RB); ++v) idx[v] = idx[v & (v - 1)] ^ prb[__ffs(v) - 1];
+}
+
 template <typename R, int RB>
 __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, const GatePassArgs a,
                                                      const DevOp *__restrict__ ops, const Phase *__restrict__ phases,
-                                                     const R *__restrict__ coef, const Cx<R> *__restrict__ mats,
+                                                     const RegStep *__restrict__ steps, const R *__restrict__ coef,
+                                                     const Cx<R> *__restrict__ mats,
                                                      const DiagBlock *__restrict__ dblocks,
                                                      const DiagMember *__restrict__ dmem) {
     constexpr int V = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t T = 1u << a.k;
-    const uint32_t nh = 1u << (a.k - a.nlow);
-    const int nb = a.db_end - a.db_begin;
-    Cx<R> *tiles = reinterpret_cast<Cx<R> *>(smem);          // two tiles: the next one streams in
-    Cx<R> *dC = tiles + 2 * T;                                // [nb][NT] diagonal-block thread factors
-    Cx<R> *dR = dC + nb * blockDim.x;                         // [nb][16] register tables
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(dR + nb * 16);
-    StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(hioff + nh);
-    uint16_t *dM = reinterpret_cast<uint16_t *>(so + (a.op_end - a.op_begin));   // [nb][NT] CZ sign patterns
-    for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
-    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef, phases, a.ph_begin, a.ph_end);
+    RA<R> *tiles = reinterpret_cast<RA<R> *>(smem);          // two tiles: the next one streams in
+    unsigned char *sm = smem + 2 * T * sizeof(RA<R>);
+    const RegLayout L = reg_layout(a, (int)sizeof(Cx<R>), false);
+    reg_setup<R, RB>(sm, L, a, ops, phases, steps, coef, dblocks, dmem, false);
     __syncthreads();
-    diag_setup<R, RB>(a, dblocks, dmem, so, dR, dC, dM, false);
-    __syncthreads();
+    const uint64_t *hioff = reinterpret_cast<const uint64_t *>(sm + L.hioff);
+    const Cx<R> *cs = reinterpret_cast<const Cx<R> *>(sm + L.cs);
+    const RegStep *st = reinterpret_cast<const RegStep *>(sm + L.steps);
+    const DiagBlock *bl = reinterpret_cast<const DiagBlock *>(sm + L.blocks);
+    const uint16_t *pbase = reinterpret_cast<const uint16_t *>(sm + L.pbase);
+    const uint16_t *prb = reinterpret_cast<const uint16_t *>(sm + L.prb);
+    const unsigned char *area = sm + L.area;
+    const int NT = blockDim.x;
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
     const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -982,48 +1277,48 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
     for (uint64_t it = 0; it < mine; ++it) {
         const uint64_t gbase = base_cur;
         base_cur = walk_next(base_cur, bw);
-        Cx<R> *tile = tiles + (it & 1) * T;
+        RA<R> *tile = tiles + (it & 1) * T;
         cp_async_wait1();
         __syncthreads();
         for (int ph = a.ph_begin; ph < a.ph_end; ++ph) {
             const Phase P = phases[ph];
-            uint32_t base, sp[V];
-            phase_index<RB>(P.rmask, a.k, base, sp);
-            Cx<R> x[V];
+            const uint32_t base = pbase[(ph - a.ph_begin) * NT + threadIdx.x];
+            uint32_t idx[V];
+            phase_slots<RB>(idx, base, prb + (ph - a.ph_begin) * 4);
+            RA<R> x[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
-            for (int o = P.op_begin; o < P.op_end;) {
-                const StagedOp<R> &x_op = so[o - a.op_begin];
-                if (x_op.ry > 0) {                   // RY on a register bit
-                    const R c = x_op.c, sn = x_op.s;
-                    switch (x_op.ry) {
-                    case 1: reg_rot<R, V, 0>(x, c, sn); break;
-                    case 2: if constexpr (RB > 1) reg_rot<R, V, 1>(x, c, sn); break;
-                    case 3: if constexpr (RB > 2) reg_rot<R, V, 2>(x, c, sn); break;
-                    case 4: if constexpr (RB > 3) reg_rot<R, V, 3>(x, c, sn); break;
-                    default: break;
+            for (int v = 0; v < V; ++v) x[v] = tile[idx[v]];
+            for (int s = P.st_begin; s < P.st_end; ++s) {
+                const RegStep S = st[s - a.st_begin];
+                if (S.type == SV_STEP_ROT) {
+                    const Cx<R> *c = cs + (S.op_begin - a.op_begin);
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) {
+                        if (!((S.a >> b) & 1)) continue;
+                        const Cx<R> k = *c++;
+                        const RotK<R> rk = rotk<R>(k.x, k.y);
+                        switch (b) {
+                        case 0: ra_rot<R, V, 0>(x, rk); break;
+                        case 1: if constexpr (RB > 1) ra_rot<R, V, 1>(x, rk); break;
+                        case 2: if constexpr (RB > 2) ra_rot<R, V, 2>(x, rk); break;
+                        case 3: if constexpr (RB > 3) ra_rot<R, V, 3>(x, rk); break;
+                        default: break;
+                        }
                     }
-                    ++o;
-                    continue;
+                } else if (S.type == SV_STEP_DIAG) {
+                    reg_diag<R, RB>(x, bl[S.a - a.db_begin], area);
+                } else {
+                    DevOp op = ops[S.a];
+                    if (has_out_target(op)) op = resolve_out(op, gbase);
+                    ra_apply_op<R, RB>(x, op, P.rmask, base, cs[S.a - a.op_begin], mats, false);
                 }
-                DevOp op = x_op.op;
-                if (has_out_target(op)) op = resolve_out(op, gbase);
-                if (op.mat <= -2) {                  // a diagonal block: all its members at once
-                    const int bi = -2 - op.mat;
-                    diag_apply<R, RB>(x, bi - a.db_begin, dR, dC, dM);
-                    o = dblocks[bi].op_end;
-                    continue;
-                }
-                const R cs[2] = {x_op.c, x_op.s};
-                op.gate = 0;
-                reg_apply<R, RB>(x, op, P.rmask, base, cs, mats, false);
-                ++o;
             }
 #pragma unroll
-            for (int v = 0; v < V; ++v) tile[swz_tile(base | sp[v])] = x[v];
+            for (int v = 0; v < V; ++v) tile[idx[v]] = x[v];
             __syncthreads();
         }
-        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = tile[swz_tile(j)];
+        const Cx<R> *tc = reinterpret_cast<const Cx<R> *>(tile);
+        for (uint32_t j = threadIdx.x; j < T; j += NT) psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = tc[swz_tile(j)];
         __syncthreads();
         if (it + 2 < mine) load_tile_async<R>(tile, psi, base_pf, hioff, a.nlow, T);
         cp_async_commit();
@@ -1034,32 +1329,31 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
 template <typename R, int RB>
 __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<R> *__restrict__ lam,
                                                     const GatePassArgs a, const DevOp *__restrict__ ops,
-                                                    const Phase *__restrict__ phases, const R *__restrict__ coef,
-                                                    const Cx<R> *__restrict__ mats, double *__restrict__ part,
-                                                    int part_stride, const DiagBlock *__restrict__ dblocks,
+                                                    const Phase *__restrict__ phases, const RegStep *__restrict__ steps,
+                                                    const R *__restrict__ coef, const Cx<R> *__restrict__ mats,
+                                                    double *__restrict__ part, int part_stride,
+                                                    const DiagBlock *__restrict__ dblocks,
                                                     const DiagMember *__restrict__ dmem) {
     constexpr int V = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t T = 1u << a.k;
-    const uint32_t nh = 1u << (a.k - a.nlow);
     const int nops = a.op_end - a.op_begin;
-    const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // shared memory: lambda tile, then the psi tile
-    const int nb = a.db_end - a.db_begin;
-    Cx<R> *tl = reinterpret_cast<Cx<R> *>(smem);
-    Cx<R> *tp = tl + T;
-    Cx<R> *dC = tp + T;                                       // [nb][NT] diagonal-block thread factors (of D^dagger)
-    Cx<R> *dR = dC + nb * blockDim.x;                         // [nb][16] register tables
-    uint64_t *hioff = reinterpret_cast<uint64_t *>(dR + nb * 16);
-    double *acc = reinterpret_cast<double *>(hioff + nh);
-    StagedOp<R> *so = reinterpret_cast<StagedOp<R> *>(acc + nops * nwarps);
-    uint16_t *dM = reinterpret_cast<uint16_t *>(so + nops);                       // [nb][NT] CZ sign patterns
-    for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) hioff[j] = deposit(j, a.hi, a.nhi);
-    for (int j = threadIdx.x; j < nops * nwarps; j += blockDim.x) acc[j] = 0.0;
-    stage_ops<R>(so, ops, a.op_begin, a.op_end, coef, phases, a.ph_begin, a.ph_end);
+    const int NT = blockDim.x, nwarps = NT >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    RA<R> *tl = reinterpret_cast<RA<R> *>(smem);           // lambda tile, then the psi tile
+    RA<R> *tp = tl + T;
+    unsigned char *sm = smem + 2 * T * sizeof(RA<R>);
+    const RegLayout L = reg_layout(a, (int)sizeof(Cx<R>), true);
+    double *acc = reinterpret_cast<double *>(sm + L.acc);
+    for (int j = threadIdx.x; j < nops * nwarps; j += NT) acc[j] = 0.0;
+    reg_setup<R, RB>(sm, L, a, ops, phases, steps, coef, dblocks, dmem, true);
     __syncthreads();
-    diag_setup<R, RB>(a, dblocks, dmem, so, dR, dC, dM, true);
-    __syncthreads();
+    const uint64_t *hioff = reinterpret_cast<const uint64_t *>(sm + L.hioff);
+    const Cx<R> *cs = reinterpret_cast<const Cx<R> *>(sm + L.cs);
+    const RegStep *st = reinterpret_cast<const RegStep *>(sm + L.steps);
+    const DiagBlock *bl = reinterpret_cast<const DiagBlock *>(sm + L.blocks);
+    const uint16_t *pbase = reinterpret_cast<const uint16_t *>(sm + L.pbase);
+    const uint16_t *prb = reinterpret_cast<const uint16_t *>(sm + L.prb);
+    const unsigned char *area = sm + L.area;
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
     const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -1072,117 +1366,145 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
             // the next tile's psi and lambda runs head for L2 while this one is processed
             const uint64_t gn = gnext;
             const uint32_t runbytes = (1u << a.nlow) * (uint32_t)sizeof(Cx<R>);
-            for (uint32_t j = threadIdx.x; j < nh; j += blockDim.x) {
+            for (uint32_t j = threadIdx.x; j < (1u << (a.k - a.nlow)); j += NT) {
                 prefetch_l2(psi + (gn | hioff[j]), runbytes);
                 prefetch_l2(lam + (gn | hioff[j]), runbytes);
             }
         }
-        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
-            const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
-            tp[swz_tile(j)] = psi[gi];
-            tl[swz_tile(j)] = lam[gi];
+        {
+            Cx<R> *tpc = reinterpret_cast<Cx<R> *>(tp), *tlc = reinterpret_cast<Cx<R> *>(tl);
+            for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
+                tpc[swz_tile(j)] = psi[gi];
+                tlc[swz_tile(j)] = lam[gi];
+            }
         }
         __syncthreads();
         for (int ph = a.ph_end - 1; ph >= a.ph_begin; --ph) {
             const Phase P = phases[ph];
-            uint32_t base, sp[V];
-            phase_index<RB>(P.rmask, a.k, base, sp);
-            Cx<R> xp[V], xl[V];
+            const uint32_t base = pbase[(ph - a.ph_begin) * NT + threadIdx.x];
+            uint32_t idx[V];
+            phase_slots<RB>(idx, base, prb + (ph - a.ph_begin) * 4);
+            RA<R> xp[V], xl[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const uint32_t si = swz_tile(base | sp[v]);
-                xp[v] = tp[si];
-                xl[v] = tl[si];
+                xp[v] = tp[idx[v]];
+                xl[v] = tl[idx[v]];
             }
-            for (int o = P.op_end - 1; o >= P.op_begin;) {
-                const StagedOp<R> &x_op = so[o - a.op_begin];
-                if (x_op.ry > 0) {                   // RY on a register bit: gradient part, then RY^dagger
-                    const R c = x_op.c, sn = -x_op.s;
-                    R g = 0;
-                    switch (x_op.ry) {
-                    case 1: g = reg_ry_adj<R, V, 0>(xp, xl, c, sn); break;
-                    case 2: if constexpr (RB > 1) g = reg_ry_adj<R, V, 1>(xp, xl, c, sn); break;
-                    case 3: if constexpr (RB > 2) g = reg_ry_adj<R, V, 2>(xp, xl, c, sn); break;
-                    case 4: if constexpr (RB > 3) g = reg_ry_adj<R, V, 3>(xp, xl, c, sn); break;
-                    default: break;
+            for (int s = P.st_end - 1; s >= P.st_begin; --s) {
+                const RegStep S = st[s - a.st_begin];
+                if (S.type == SV_STEP_ROT) {
+                    // every RY of the step: gradient part at the step's end (they commute), then RY^dagger
+                    R g[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) {
+                        if (!((S.a >> b) & 1)) continue;
+                        switch (b) {
+                        case 0: g[0] = ra_ry_grad<R, V, 0>(xp, xl); break;
+                        case 1: if constexpr (RB > 1) g[1] = ra_ry_grad<R, V, 1>(xp, xl); break;
+                        case 2: if constexpr (RB > 2) g[2] = ra_ry_grad<R, V, 2>(xp, xl); break;
+                        case 3: if constexpr (RB > 3) g[3] = ra_ry_grad<R, V, 3>(xp, xl); break;
+                        default: break;
+                        }
                     }
-                    g = warp_sum<R>(g);
-                    if (lane == 0) acc[(o - a.op_begin) * nwarps + warp] += (double)g;
-                    --o;
-                    continue;
-                }
-                DevOp op = x_op.op;
-                if (has_out_target(op)) op = resolve_out(op, gbase);
-                if (op.mat <= -2) {
-                    // a diagonal block: every member's generator expectation
-                    // at the block's end (Z commutes with the block), then
-                    // D^dagger on both register sets
-                    const int bi = -2 - op.mat;
-                    const DiagBlock B = dblocks[bi];
+                    const R tot = warp_sum4<R>(g[0], g[1], g[2], g[3]);
+                    const Cx<R> *c = cs + (S.op_begin - a.op_begin);
+                    int o = S.op_begin - a.op_begin;
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) {
+                        if (!((S.a >> b) & 1)) continue;
+                        if (lane == 8 * b) acc[o * nwarps + warp] += (double)tot;
+                        ++o;
+                        const Cx<R> k = *c++;
+                        const RotK<R> rk = rotk<R>(k.x, k.y);
+                        switch (b) {
+                        case 0: ra_rot<R, V, 0>(xp, rk); ra_rot<R, V, 0>(xl, rk); break;
+                        case 1: if constexpr (RB > 1) { ra_rot<R, V, 1>(xp, rk); ra_rot<R, V, 1>(xl, rk); } break;
+                        case 2: if constexpr (RB > 2) { ra_rot<R, V, 2>(xp, rk); ra_rot<R, V, 2>(xl, rk); } break;
+                        case 3: if constexpr (RB > 3) { ra_rot<R, V, 3>(xp, rk); ra_rot<R, V, 3>(xl, rk); } break;
+                        default: break;
+                        }
+                    }
+                } else if (S.type == SV_STEP_DIAG) {
+                    // every RZ member's generator expectation at the block's end (Z
+                    // commutes with the block), then D^dagger on both register sets
+                    const DiagBlock B = bl[S.a - a.db_begin];
                     R tv[V], tot = 0;
 #pragma unroll
                     for (int v = 0; v < V; ++v) {
-                        tv[v] = xl[v].x * xp[v].y - xl[v].y * xp[v].x;
+                        tv[v] = ra_imdot<R>(xl[v], xp[v]);
                         tot += tv[v];
                     }
-                    R sb[RB];
+                    if (B.kind == 0) {
+                        R sb[4] = {0, 0, 0, 0};
 #pragma unroll
-                    for (int b = 0; b < RB; ++b) {
-                        R acc_b = 0;
+                        for (int b = 0; b < RB; ++b) {
+                            R acc_b = 0;
 #pragma unroll
-                        for (int v = 0; v < V; ++v) acc_b += ((v >> b) & 1) ? -tv[v] : tv[v];
-                        sb[b] = acc_b;
-                    }
-                    for (int mi = B.m_begin; mi < B.m_end; ++mi) {
-                        const DiagMember m = dmem[mi];
-                        R g;
-                        if (m.type == SV_DM_REG_RZ) {
-                            g = sb[0];
-#pragma unroll
-                            for (int b = 1; b < RB; ++b) g = (m.a == b) ? sb[b] : g;
-                        } else if (m.type == SV_DM_THR_RZ) {
-                            g = ((base >> m.a) & 1u) ? -tot : tot;
-                        } else {
-                            continue;
+                            for (int v = 0; v < V; ++v) acc_b += ((v >> b) & 1) ? -tv[v] : tv[v];
+                            sb[b] = acc_b;
                         }
-                        g = warp_sum<R>(g);
-                        if (lane == 0) acc[(m.op - a.op_begin) * nwarps + warp] += (double)g;
+                        const R red = warp_sum4<R>(sb[0], sb[1], sb[2], sb[3]);
+                        for (int mi = B.m_begin; mi < B.m_end; ++mi) {
+                            const DiagMember m = dmem[mi];
+                            if (m.type == SV_DM_REG_RZ && lane == 8 * m.a)
+                                acc[(m.op - a.op_begin) * nwarps + warp] += (double)red;
+                        }
+                    } else {
+                        // thread RZ members: +-tot by the thread's bit, four at a time
+                        for (int m0 = B.m_begin; m0 < B.m_end; m0 += 4) {
+                            R vals[4] = {0, 0, 0, 0};
+                            int opi[4] = {-1, -1, -1, -1};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                if (m0 + j >= B.m_end) break;
+                                const DiagMember m = dmem[m0 + j];
+                                if (m.type != SV_DM_THR_RZ) continue;
+                                vals[j] = ((base >> m.a) & 1u) ? -tot : tot;
+                                opi[j] = m.op - a.op_begin;
+                            }
+                            const R red = warp_sum4<R>(vals[0], vals[1], vals[2], vals[3]);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * nwarps + warp] += (double)red;
+                        }
                     }
-                    diag_apply<R, RB>(xp, bi - a.db_begin, dR, dC, dM);
-                    diag_apply<R, RB>(xl, bi - a.db_begin, dR, dC, dM);
-                    o = B.op_begin - 1;
-                    continue;
+                    reg_diag<R, RB>(xp, B, area);
+                    reg_diag<R, RB>(xl, B, area);
+                } else {
+                    DevOp op = ops[S.a];
+                    if (has_out_target(op)) op = resolve_out(op, gbase);
+                    R g = ra_adjoint_op<R, RB>(xp, xl, op, P.rmask, base, cs[S.a - a.op_begin], mats);
+                    if (has_param(op.kind)) {
+                        g = warp_sum<R>(g);
+                        if (lane == 0) acc[(S.a - a.op_begin) * nwarps + warp] += (double)g;
+                    }
                 }
-                const R cs[2] = {x_op.c, x_op.s};
-                op.gate = 0;
-                R g = reg_adjoint<R, RB>(xp, xl, op, P.rmask, base, cs, mats);
-                if (has_param(op.kind)) {
-                    g = warp_sum<R>(g);
-                    if (lane == 0) acc[(o - a.op_begin) * nwarps + warp] += (double)g;
-                }
-                --o;
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const uint32_t si = swz_tile(base | sp[v]);
-                tp[si] = xp[v];
-                tl[si] = xl[v];
+                tp[idx[v]] = xp[v];
+                tl[idx[v]] = xl[v];
             }
             __syncthreads();
         }
-        for (uint32_t j = threadIdx.x; j < T; j += blockDim.x) {
-            const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
-            psi[gi] = tp[swz_tile(j)];
-            lam[gi] = tl[swz_tile(j)];
+        {
+            const Cx<R> *tpc = reinterpret_cast<const Cx<R> *>(tp), *tlc = reinterpret_cast<const Cx<R> *>(tl);
+            for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
+                psi[gi] = tpc[swz_tile(j)];
+                lam[gi] = tlc[swz_tile(j)];
+            }
         }
         __syncthreads();
     }
-    for (int o = threadIdx.x; o < nops; o += blockDim.x) {
+    for (int o = threadIdx.x; o < nops; o += NT) {
         double tsum = 0.0;
         for (int w = 0; w < nwarps; ++w) tsum += acc[o * nwarps + w];
         part[(size_t)blockIdx.x * part_stride + a.op_begin + o] = tsum;
     }
 }
+#undef SV_RB_SWITCH
 
 // -------------------------------------------------------------------- K-QR --
 struct SwapArgs {
@@ -2659,20 +2981,25 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
 
 template <typename R>
 cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePassArgs &a, const DevOp *ops,
-                              const Phase *phases, const void *coef, const void *mats, const DiagBlock *dblocks,
-                              const DiagMember *dmem) {
-    const size_t nb = (size_t)(a.db_end - a.db_begin);
-    const size_t sm = 2 * ((size_t)1 << a.k) * sizeof(Cx<R>) + ((size_t)1 << (a.k - a.nlow)) * 8 +
-                      nb * (512 + 16) * sizeof(Cx<R>) + nb * 512 * 2 +
-                      (size_t)(a.op_end - a.op_begin) * sizeof(StagedOp<R>) + 64;
+                              const Phase *phases, const RegStep *steps, const void *coef, const void *mats,
+                              const DiagBlock *dblocks, const DiagMember *dmem) {
+    const size_t sm = gate_reg_smem(sizeof(R) == 4 ? SV_C64 : SV_C128, a);
     switch (a.k - 9) {
 #define SV_GR(RB)                                                                                            \
     case RB:                                                                                                 \
         allow_smem(k_gate_reg<R, RB>, sm);                                                                   \
-        k_gate_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, a, ops, phases, (const R *)coef,              \
-                                                 (const Cx<R> *)mats, dblocks, dmem);                        \
+        k_gate_reg<R, RB><<<grid, kRegThreads, sm, st>>>((Cx<R> *)psi, a, ops, phases, steps, (const R *)coef, \
+                                                         (const Cx<R> *)mats, dblocks, dmem);                \
         break;
-        SV_GR(2) SV_GR(3) SV_GR(4)
+        SV_GR(2) SV_GR(3)
+    case 4:   // complex128 tiles hold at most 2^12 amplitudes
+        if constexpr (sizeof(R) == 4) {
+            allow_smem(k_gate_reg<R, 4>, sm);
+            k_gate_reg<R, 4><<<grid, kRegThreads, sm, st>>>((Cx<R> *)psi, a, ops, phases, steps, (const R *)coef,
+                                                            (const Cx<R> *)mats, dblocks, dmem);
+            break;
+        }
+        return cudaErrorInvalidValue;
 #undef SV_GR
     default:
         return cudaErrorInvalidValue;
@@ -2682,21 +3009,28 @@ cudaError_t gate_reg_dispatch(cudaStream_t st, int grid, void *psi, const GatePa
 
 template <typename R>
 cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
-                             const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
-                             int part_stride, const DiagBlock *dblocks, const DiagMember *dmem) {
-    const size_t tile = ((size_t)1 << a.k) * sizeof(Cx<R>);
-    const size_t nb = (size_t)(a.db_end - a.db_begin);
-    const size_t rest = ((size_t)1 << (a.k - a.nlow)) * 8 + (size_t)(a.op_end - a.op_begin) * (16 * 8 + sizeof(StagedOp<R>)) +
-                        nb * (512 + 16) * sizeof(Cx<R>) + nb * 512 * 2 + 64;
-    const size_t sm = 2 * tile + rest;
+                             const DevOp *ops, const Phase *phases, const RegStep *steps, const void *coef,
+                             const void *mats, double *part, int part_stride, const DiagBlock *dblocks,
+                             const DiagMember *dmem) {
+    const size_t sm = adj_reg_smem(sizeof(R) == 4 ? SV_C64 : SV_C128, a);
     switch (a.k - 9) {
 #define SV_AR(RB)                                                                                            \
     case RB:                                                                                                 \
         allow_smem(k_adj_reg<R, RB>, sm);                                                                    \
-        k_adj_reg<R, RB><<<grid, 512, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases, (const R *)coef, \
-                                                (const Cx<R> *)mats, part, part_stride, dblocks, dmem);      \
+        k_adj_reg<R, RB><<<grid, kRegThreads, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases, steps,   \
+                                                        (const R *)coef, (const Cx<R> *)mats, part, part_stride, \
+                                                        dblocks, dmem);                                      \
         break;
-        SV_AR(2) SV_AR(3) SV_AR(4)
+        SV_AR(2) SV_AR(3)
+    case 4:
+        if constexpr (sizeof(R) == 4) {
+            allow_smem(k_adj_reg<R, 4>, sm);
+            k_adj_reg<R, 4><<<grid, kRegThreads, sm, st>>>((Cx<R> *)psi, (Cx<R> *)lam, a, ops, phases, steps,
+                                                           (const R *)coef, (const Cx<R> *)mats, part, part_stride,
+                                                           dblocks, dmem);
+            break;
+        }
+        return cudaErrorInvalidValue;
 #undef SV_AR
     default:
         return cudaErrorInvalidValue;
@@ -2704,19 +3038,32 @@ cudaError_t adj_reg_dispatch(cudaStream_t st, int grid, void *psi, void *lam, co
     return cudaGetLastError();
 }
 
+size_t gate_reg_smem(sv_dtype dt, const GatePassArgs &a) {
+    const int amp = dt == SV_C64 ? 8 : 16;
+    return 2 * ((size_t)1 << a.k) * amp + reg_layout(a, amp, false).total;
+}
+
+size_t adj_reg_smem(sv_dtype dt, const GatePassArgs &a) {
+    const int amp = dt == SV_C64 ? 8 : 16;
+    return 2 * ((size_t)1 << a.k) * amp + reg_layout(a, amp, true).total;
+}
+
 cudaError_t launch_gate_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, const GatePassArgs &a,
-                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats,
-                            const DiagBlock *dblocks, const DiagMember *dmem) {
-    if (dt == SV_C64) return gate_reg_dispatch<float>(st, grid, psi, a, ops, phases, coef, mats, dblocks, dmem);
-    return gate_reg_dispatch<double>(st, grid, psi, a, ops, phases, coef, mats, dblocks, dmem);
+                            const DevOp *ops, const Phase *phases, const RegStep *steps, const void *coef,
+                            const void *mats, const DiagBlock *dblocks, const DiagMember *dmem) {
+    if (dt == SV_C64) return gate_reg_dispatch<float>(st, grid, psi, a, ops, phases, steps, coef, mats, dblocks, dmem);
+    return gate_reg_dispatch<double>(st, grid, psi, a, ops, phases, steps, coef, mats, dblocks, dmem);
 }
 
 cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
-                           const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
-                           int part_stride, const DiagBlock *dblocks, const DiagMember *dmem) {
+                           const DevOp *ops, const Phase *phases, const RegStep *steps, const void *coef,
+                           const void *mats, double *part, int part_stride, const DiagBlock *dblocks,
+                           const DiagMember *dmem) {
     if (dt == SV_C64)
-        return adj_reg_dispatch<float>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride, dblocks, dmem);
-    return adj_reg_dispatch<double>(st, grid, psi, lam, a, ops, phases, coef, mats, part, part_stride, dblocks, dmem);
+        return adj_reg_dispatch<float>(st, grid, psi, lam, a, ops, phases, steps, coef, mats, part, part_stride,
+                                       dblocks, dmem);
+    return adj_reg_dispatch<double>(st, grid, psi, lam, a, ops, phases, steps, coef, mats, part, part_stride,
+                                    dblocks, dmem);
 }
 
 cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi, void *lam,

@@ -15,6 +15,8 @@ struct GatePassArgs {
     int n, k, nlow, nhi, nout, op_begin, op_end;
     int ph_begin, ph_end;    // register phases (register-blocked pass), else -1
     int db_begin, db_end;    // diagonal blocks of the pass
+    int st_begin, st_end;    // steps of the pass's register phases
+    int area;                // bytes of the diagonal-block data
     int8_t hi[40];
     int8_t out[64];
 };
@@ -85,13 +87,19 @@ cudaError_t launch_gate_pass(sv_dtype dt, cudaStream_t st, int grid, int threads
 cudaError_t launch_adj_pass(sv_dtype dt, cudaStream_t st, int grid, int threads, void *psi, void *lam,
                             const GatePassArgs &a, const DevOp *ops, const void *coef, const void *mats,
                             double *part, int part_stride);
-// Register-blocked passes (512 threads; a.ph_begin >= 0, 11 <= k <= 13).
+// Register-blocked passes (512 threads; a.ph_begin >= 0, 11 <= k <= 13): the
+// phases' steps (RegStep) are executed in order (forward) or in reverse
+// (adjoint); part receives the FP64 gradient partials of every operation.
 cudaError_t launch_gate_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, const GatePassArgs &a,
-                            const DevOp *ops, const Phase *phases, const void *coef, const void *mats,
-                            const DiagBlock *dblocks, const DiagMember *dmem);
+                            const DevOp *ops, const Phase *phases, const RegStep *steps, const void *coef,
+                            const void *mats, const DiagBlock *dblocks, const DiagMember *dmem);
 cudaError_t launch_adj_reg(sv_dtype dt, cudaStream_t st, int grid, void *psi, void *lam, const GatePassArgs &a,
-                           const DevOp *ops, const Phase *phases, const void *coef, const void *mats, double *part,
-                           int part_stride, const DiagBlock *dblocks, const DiagMember *dmem);
+                           const DevOp *ops, const Phase *phases, const RegStep *steps, const void *coef,
+                           const void *mats, double *part, int part_stride, const DiagBlock *dblocks,
+                           const DiagMember *dmem);
+// Shared memory of a register-blocked pass (forward / adjoint).
+size_t gate_reg_smem(sv_dtype dt, const GatePassArgs &a);
+size_t adj_reg_smem(sv_dtype dt, const GatePassArgs &a);
 // In-place swap of disjoint physical bit pairs (pairs[2i], pairs[2i+1]).
 cudaError_t launch_bitswap(sv_dtype dt, cudaStream_t st, void *psi, int n, const int32_t *pairs,
                            int npairs, int blocks_per_sm);

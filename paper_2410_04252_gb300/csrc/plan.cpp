@@ -485,6 +485,7 @@ void plan_phases(QsuPlan &P) {
             for (uint32_t fr = all & ~Rm; __builtin_popcount(Rm) < r && fr; fr &= fr - 1) Rm |= fr & (0u - fr);
             Phase ph;
             ph.rmask = Rm;
+            ph.st_begin = ph.st_end = 0;
             ph.op_begin = gp.op_begin + (int32_t)out.size();
             uint32_t av = all;
             next.clear();
@@ -506,103 +507,206 @@ void plan_phases(QsuPlan &P) {
     }
 }
 
-// Diagonal blocks: inside each register phase, every run of >= 2
-// consecutive RZ / CZ operations becomes one block (they commute, so the run
-// is one diagonal operator; in the adjoint sweep every member's generator
-// expectation is taken at the run's end, since Z commutes with the run).
-// Inside a phase, diagonal operations are delayed past later non-diagonal
-// operations on other qubits (disjoint supports commute, diagonal operations
-// commute with each other), so that they gather into long runs; a
-// non-diagonal operation that shares a qubit with a delayed diagonal one
-// first flushes the delayed ones.  The order stays a valid schedule (C1).
+// Steps of the register phases.  Inside a phase two operations on disjoint
+// tile bits commute, and so do two diagonal operations (RZ, CZ) on any bits;
+// every topological order of the "does not commute" relation applies the
+// same operator.  Diagonal gates on thread bits only (no register bit) commute
+// with every operation of the phase: they form one thread block at the
+// phase's end.  The rest is rescheduled as a list of steps: all ready RY
+// gates (distinct register bits) form one ROT step; when none is ready, other
+// non-diagonal operations go one by one; when only diagonal ones are ready,
+// all of them form one run, so that diagonal gates are delayed as long as
+// possible and gather into few runs.  A run worth it becomes a register
+// block, else its operations go one by one.  Blocks are made while the
+// pass's shared memory allows.  In the adjoint sweep every RZ of a block
+// takes its generator expectation at the block's end (Z commutes with the
+// block), every RY of a ROT step at the step's end, and every RZ of a thread
+// block anywhere in the phase (it commutes with the whole phase).
 bool in_tile_diag(const DevOp &d) {
     return diag_kind(d.kind) && d.t[0] < kOutTarget && (d.kind != SV_CZ || d.t[1] < kOutTarget);
 }
 
-void cluster_diagonals(QsuPlan &P, const Phase &F) {
+// A run is worth a register block when its members one by one cost more
+// than one table lookup and complex product per amplitude: RZ ~ one complex
+// product per amplitude, CZ ~ a quarter.
+bool diag_run_pays(const std::vector<DevOp> &run) {
+    int rz = 0, cz = 0;
+    for (auto &d : run) (d.kind == SV_RZ ? rz : cz)++;
+    return 4 * rz + cz >= 6;
+}
+
+void plan_steps(QsuPlan &P, int max_diag, int amp) {
     auto tm = [](const DevOp &d) {
         uint32_t m = 0;
         const int nq = d.kind == SV_CZ ? 2 : 1;
         for (int i = 0; i < nq; ++i)
-            if (d.t[i] < kOutTarget) m |= 1u << d.t[i];
+            if (d.t[i] >= 0 && d.t[i] < kOutTarget) m |= 1u << d.t[i];
         return m;
     };
-    std::vector<DevOp> out, pend;
-    uint32_t pmask = 0;
-    for (int o = F.op_begin; o < F.op_end; ++o) {
-        const DevOp &d = P.ops[o];
-        if (in_tile_diag(d)) {
-            pend.push_back(d);
-            pmask |= tm(d);
-            continue;
-        }
-        if (tm(d) & pmask) {
-            out.insert(out.end(), pend.begin(), pend.end());
-            pend.clear();
-            pmask = 0;
-        }
-        out.push_back(d);
-    }
-    out.insert(out.end(), pend.begin(), pend.end());
-    std::copy(out.begin(), out.end(), P.ops.begin() + F.op_begin);
-}
-
-// A run is worth a block when its members cost more than one block
-// application (about two complex products per amplitude): RZ ~ one complex
-// product per amplitude, CZ ~ a quarter.
-bool diag_run_pays(const QsuPlan &P, int o, int e) {
-    int rz = 0, cz = 0;
-    for (int u = o; u < e; ++u) (P.ops[u].kind == SV_RZ ? rz : cz)++;
-    return 4 * rz + cz > 10;
-}
-
-void plan_diag_blocks(QsuPlan &P, int max_diag) {
     for (auto &gp : P.passes) {
         gp.db_begin = gp.db_end = (int32_t)P.dblocks.size();
         if (gp.ph_begin < 0) continue;
+        const int nops = gp.op_end - gp.op_begin;
+        int budget = kRegSmemLimit - reg_pass_fixed_bytes(gp.k, gp.nlow, nops, nops, gp.ph_end - gp.ph_begin, amp);
+        int area = 0;   // bytes of the pass's block area handed out so far
+        auto take_block = [&](int kind) {
+            const int need = diag_block_bytes(kind, gp.k, amp);
+            if ((int)P.dblocks.size() - gp.db_begin >= max_diag || need > budget) return -1;
+            budget -= need;
+            const int off = area;
+            area += need;
+            return off;
+        };
         for (int ph = gp.ph_begin; ph < gp.ph_end; ++ph) {
-            const Phase &F = P.phases[ph];
-            cluster_diagonals(P, F);
-            int o = F.op_begin;
-            while (o < F.op_end) {
-                if (!in_tile_diag(P.ops[o])) { ++o; continue; }
-                int e = o;
-                while (e < F.op_end && in_tile_diag(P.ops[e])) ++e;
-                if (diag_run_pays(P, o, e) && (int)P.dblocks.size() - gp.db_begin < max_diag) {
-                    DiagBlock B;
-                    B.op_begin = o;
-                    B.op_end = e;
-                    B.m_begin = (int32_t)P.dmembers.size();
-                    B.rmask = F.rmask;
-                    B.pad = 0;
-                    const int bi = (int)P.dblocks.size();
-                    auto regidx = [&](int t) { return __builtin_popcount(F.rmask & ((1u << t) - 1u)); };
-                    for (int u = o; u < e; ++u) {
-                        DevOp &d = P.ops[u];
-                        DiagMember m;
-                        m.op = u;
-                        m.a = m.b = 0;
-                        if (d.kind == SV_RZ) {
-                            const int t = d.t[0];
-                            if (F.rmask >> t & 1u) { m.type = SV_DM_REG_RZ; m.a = regidx(t); }
-                            else { m.type = SV_DM_THR_RZ; m.a = t; }
-                        } else {
-                            const int t0 = d.t[0], t1 = d.t[1];
-                            const bool r0 = F.rmask >> t0 & 1u, r1 = F.rmask >> t1 & 1u;
-                            if (r0 && r1) { m.type = SV_DM_REG_CZ; m.a = regidx(t0); m.b = regidx(t1); }
-                            else if (!r0 && !r1) { m.type = SV_DM_THR_CZ; m.a = t0; m.b = t1; }
-                            else { m.type = SV_DM_MIX_CZ; m.a = regidx(r0 ? t0 : t1); m.b = r0 ? t1 : t0; }
-                        }
-                        d.mat = -2 - bi;
-                        P.dmembers.push_back(m);
-                    }
-                    B.m_end = (int32_t)P.dmembers.size();
-                    P.dblocks.push_back(B);
-                }
-                o = e;
+            Phase &F = P.phases[ph];
+            F.st_begin = (int32_t)P.steps.size();
+            const std::vector<DevOp> all(P.ops.begin() + F.op_begin, P.ops.begin() + F.op_end);
+            // thread-only diagonal operations: one thread block if room
+            std::vector<DevOp> in, thr;
+            for (auto &d : all) {
+                if (in_tile_diag(d) && !(tm(d) & F.rmask)) thr.push_back(d);
+                else in.push_back(d);
             }
+            int thr_off = -1;
+            if (!thr.empty()) {
+                thr_off = take_block(1);
+                if (thr_off < 0) {
+                    in = all;
+                    thr.clear();
+                }
+            }
+            const int N = (int)in.size();
+            std::vector<uint32_t> m(N);
+            std::vector<char> dg(N), ry(N), done(N, 0);
+            for (int i = 0; i < N; ++i) {
+                m[i] = tm(in[i]);
+                dg[i] = diag_kind(in[i].kind);
+                ry[i] = in[i].kind == SV_RY && in[i].t[0] < kOutTarget && (F.rmask >> in[i].t[0] & 1u);
+            }
+            std::vector<int> npred(N, 0);
+            std::vector<std::vector<int>> succ(N);
+            for (int j = 0; j < N; ++j)
+                for (int i = 0; i < j; ++i)
+                    if ((m[i] & m[j]) && !(dg[i] && dg[j])) {
+                        ++npred[j];
+                        succ[i].push_back(j);
+                    }
+            std::vector<DevOp> out;
+            auto regidx = [&](int t) { return __builtin_popcount(F.rmask & ((1u << t) - 1u)); };
+            auto emit_op = [&](const DevOp &d) { out.push_back(d); };
+            auto emit = [&](int i) {
+                done[i] = 1;
+                for (int j : succ[i]) --npred[j];
+                emit_op(in[i]);
+            };
+            auto push_op = [&](int i) {
+                RegStep st;
+                st.type = SV_STEP_OP;
+                st.op_begin = F.op_begin + (int32_t)out.size();
+                st.op_end = st.op_begin + 1;
+                st.a = st.op_begin;
+                emit(i);
+                P.steps.push_back(st);
+            };
+            auto member = [&](const DevOp &d, int pos) {
+                DiagMember dm;
+                dm.op = F.op_begin + pos;
+                dm.a = dm.b = 0;
+                if (d.kind == SV_RZ) {
+                    const int t = d.t[0];
+                    if (F.rmask >> t & 1u) { dm.type = SV_DM_REG_RZ; dm.a = regidx(t); }
+                    else { dm.type = SV_DM_THR_RZ; dm.a = t; }
+                } else {
+                    const int t0 = d.t[0], t1 = d.t[1];
+                    const bool r0 = F.rmask >> t0 & 1u, r1 = F.rmask >> t1 & 1u;
+                    if (r0 && r1) { dm.type = SV_DM_REG_CZ; dm.a = regidx(t0); dm.b = regidx(t1); }
+                    else if (!r0 && !r1) { dm.type = SV_DM_THR_CZ; dm.a = t0; dm.b = t1; }
+                    else { dm.type = SV_DM_MIX_CZ; dm.a = regidx(r0 ? t0 : t1); dm.b = r0 ? t1 : t0; }
+                }
+                return dm;
+            };
+            // emits a block of the given ops (positions follow in `out`)
+            auto push_block = [&](int kind, int off, const std::vector<DevOp> &ops, const std::vector<int> &idx) {
+                const int bi = (int)P.dblocks.size();
+                DiagBlock B;
+                B.op_begin = F.op_begin + (int32_t)out.size();
+                B.m_begin = (int32_t)P.dmembers.size();
+                B.rmask = F.rmask;
+                B.kind = kind;
+                B.smem = off;
+                B.pad = 0;
+                for (size_t u = 0; u < ops.size(); ++u) {
+                    P.dmembers.push_back(member(ops[u], (int)out.size()));
+                    if (idx.empty()) emit_op(ops[u]);
+                    else emit(idx[u]);
+                    out.back().mat = -2 - bi;
+                }
+                B.op_end = F.op_begin + (int32_t)out.size();
+                B.m_end = (int32_t)P.dmembers.size();
+                P.dblocks.push_back(B);
+                RegStep st;
+                st.type = SV_STEP_DIAG;
+                st.a = bi;
+                st.op_begin = B.op_begin;
+                st.op_end = B.op_end;
+                P.steps.push_back(st);
+            };
+            int left = N;
+            while (left > 0) {
+                std::vector<int> rys, others, diags;
+                for (int i = 0; i < N; ++i) {
+                    if (done[i] || npred[i]) continue;
+                    if (ry[i]) rys.push_back(i);
+                    else if (dg[i]) diags.push_back(i);
+                    else others.push_back(i);
+                }
+                if (!rys.empty()) {
+                    std::sort(rys.begin(), rys.end(), [&](int a, int b) { return in[a].t[0] < in[b].t[0]; });
+                    RegStep st;
+                    st.type = SV_STEP_ROT;
+                    st.op_begin = F.op_begin + (int32_t)out.size();
+                    st.a = 0;
+                    for (int i : rys) {
+                        st.a |= 1 << regidx(in[i].t[0]);
+                        emit(i);
+                    }
+                    st.op_end = F.op_begin + (int32_t)out.size();
+                    P.steps.push_back(st);
+                    left -= (int)rys.size();
+                    continue;
+                }
+                if (!others.empty()) {
+                    for (int i : others) push_op(i);
+                    left -= (int)others.size();
+                    continue;
+                }
+                // diagonal operations only: blockable ones as one run, the rest one by one
+                std::vector<int> run;
+                for (int i : diags) {
+                    const DevOp &d = in[i];
+                    // a thread-only member cannot go into a register block
+                    if (in_tile_diag(d) && (tm(d) & F.rmask)) run.push_back(i);
+                    else push_op(i);
+                }
+                left -= (int)diags.size();
+                if (run.empty()) continue;
+                std::vector<DevOp> rops;
+                for (int i : run) rops.push_back(in[i]);
+                const int off = diag_run_pays(rops) ? take_block(0) : -1;
+                if (off < 0) {
+                    for (int i : run) push_op(i);
+                    continue;
+                }
+                push_block(0, off, rops, run);
+            }
+            if (!thr.empty()) push_block(1, thr_off, thr, {});
+            std::copy(out.begin(), out.end(), P.ops.begin() + F.op_begin);
+            F.st_end = (int32_t)P.steps.size();
         }
         gp.db_end = (int32_t)P.dblocks.size();
+        gp.st_begin = P.phases[gp.ph_begin].st_begin;
+        gp.st_end = P.phases[gp.ph_end - 1].st_end;
+        gp.area = area;
     }
 }
 
@@ -1006,7 +1110,7 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
     int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
     plan_gate_passes(P, ops, k, o.low_bits, o.fuse_max, o.diag_exempt);
     plan_phases(P);
-    plan_diag_blocks(P, std::min(o.max_diag, kMaxPassDiag));
+    plan_steps(P, std::min(o.max_diag, kMaxPassDiag), o.amp_bytes);
     return "";
 }
 

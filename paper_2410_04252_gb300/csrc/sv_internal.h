@@ -56,19 +56,27 @@ struct GatePass {
     int32_t op_begin = 0, op_end = 0; // into QsuPlan::ops
     int32_t ph_begin = -1, ph_end = -1;  // register phases (register-blocked passes), else -1
     int32_t db_begin = 0, db_end = 0;    // diagonal blocks of the pass (register-blocked passes)
+    int32_t st_begin = 0, st_end = 0;    // steps of the pass's phases
+    int32_t area = 0;                    // bytes of the pass's diagonal-block data (shared memory)
 };
 
 // A run of consecutive diagonal operations (RZ, CZ) inside one register
-// phase, applied as one diagonal operator: the phase factor of a register
-// amplitude is a thread constant (operations on thread bits) times a table
-// entry indexed by the register bits (operations on register bits), with a
-// per-thread sign pattern for CZs between a register and a thread bit.
-// Every member op carries mat = -2 - (block index).
+// phase, applied as one diagonal operator.  Two kinds:
+//  * register block (kind 0): RZ / CZ on register bits and CZs between a
+//    register and a thread bit; the factor of register amplitude v of a
+//    thread is a table entry T[v][zm], zm = the register bits on which the
+//    thread's register-thread CZs put a Z (a per-thread constant);
+//  * thread block (kind 1): RZ / CZ on thread bits only; one complex factor
+//    per thread for all its amplitudes.  Such gates commute with everything
+//    else in the phase, so all of a phase's go into one thread block.
+// Every member op carries mat = -2 - (block index).  smem: byte offset of
+// the block's data in the kernels' block area (tables and per-thread data).
 struct DiagBlock {
     int32_t op_begin, op_end;     // member ops (consecutive in QsuPlan::ops)
     int32_t m_begin, m_end;       // into QsuPlan::dmembers
     uint32_t rmask;               // register tile bits of the phase
-    int32_t pad;
+    int32_t kind;                 // 0 register block, 1 thread block
+    int32_t smem, pad;
 };
 enum { SV_DM_REG_RZ = 0, SV_DM_THR_RZ = 1, SV_DM_REG_CZ = 2, SV_DM_THR_CZ = 3, SV_DM_MIX_CZ = 4 };
 struct DiagMember {
@@ -76,7 +84,8 @@ struct DiagMember {
     int32_t a, b;     // register index (0..r-1) or tile bit, per type; MIX_CZ: a register, b tile bit
     int32_t op;       // index into QsuPlan::ops (coefficient and gradient slot)
 };
-constexpr int kMaxPassDiag = 10;       // diagonal blocks per register-blocked pass
+constexpr int kMaxPassDiag = 24;       // diagonal blocks per register-blocked pass
+constexpr int kRegThreads = 512;       // CTA size of register-blocked passes (r = k - 9)
 
 // A register phase of a register-blocked pass: each thread holds the
 // amplitudes spanned by the tile bits in rmask; ops [op_begin, op_end) are
@@ -85,8 +94,35 @@ constexpr int kMaxPassDiag = 10;       // diagonal blocks per register-blocked p
 struct Phase {
     uint32_t rmask;
     int32_t op_begin, op_end;
+    int32_t st_begin, st_end;   // steps of the phase (QsuPlan::steps)
 };
-constexpr int kRegThreads = 512;      // CTA size of register-blocked passes (r = k - 9)
+
+// A step of a register phase, executed as one unit by the register-blocked
+// kernels.  ROT: RY gates on distinct register bits (they commute), ops
+// [op_begin, op_end) ordered by register bit, a = the register-bit mask.
+// DIAG: a diagonal block (a = its index in QsuPlan::dblocks), ops = its
+// members.  OP: one operation (a = op_begin), applied by the generic code.
+enum { SV_STEP_ROT = 0, SV_STEP_DIAG = 1, SV_STEP_OP = 2 };
+// Shared memory of a register-blocked pass of k staged bits (512 threads,
+// amplitudes of amp bytes): the block area needs at most this much beyond
+// the tiles, tables and accumulators, and each block takes
+// diag_block_bytes() of it.
+constexpr int kRegSmemLimit = 226 * 1024;
+inline int diag_block_bytes(int kind, int k, int amp) {
+    const int V = 1 << (k - 9);
+    return kind == 0 ? V * V * amp + 512 : 512 * amp;
+}
+inline int reg_pass_fixed_bytes(int k, int nlow, int nops, int nsteps, int nphases, int amp) {
+    // adjoint (the larger): psi and lambda tiles, high offsets, (c, s) per op,
+    // steps, block headers, per-phase thread bases and register offsets,
+    // FP64 per-warp gradient slots, alignment
+    return 2 * (1 << k) * amp + 8 * (1 << (k - nlow)) + nops * amp + 16 * nsteps + 32 * kMaxPassDiag +
+           nphases * (2 * kRegThreads + 8) + nops * (kRegThreads / 32) * 8 + 256;
+}
+struct RegStep {
+    int32_t type, a;
+    int32_t op_begin, op_end;
+};
 
 struct QsuPlan {
     int n = 0, g = 0, nL = 0;
@@ -95,6 +131,7 @@ struct QsuPlan {
     std::vector<GatePass> passes;
     std::vector<DevOp> ops;           // pass operations, pass by pass, in execution order
     std::vector<Phase> phases;        // register phases of register-blocked passes
+    std::vector<RegStep> steps;       // steps of the register phases
     std::vector<DiagBlock> dblocks;   // diagonal blocks of register phases
     std::vector<DiagMember> dmembers;
     std::vector<int32_t> init_l2p, final_l2p;
@@ -151,6 +188,7 @@ struct PlanOptions {
     int fuse_max = 0;            // gate operations per gate pass (0 = as many as fit)
     int hier_intra = -1;         // >= 0: hierarchical tiling (Alg. 4/5) with this many intra qubits
     int max_diag = kMaxPassDiag; // diagonal blocks per register-blocked pass (shared-memory budget)
+    int amp_bytes = 8;           // 8 complex64, 16 complex128 (shared-memory budget of the blocks)
     bool diag_exempt = false;    // QSU: diagonal gates (RZ, CZ) never ask for a QR (per-chunk phases)
     // One greedy step of Alg. 6 done elsewhere (on the device): given the
     // distinct X/Y supports xs with remaining weights w, return the rank of
