@@ -93,6 +93,8 @@ GatePassArgs gate_args(int n, const GatePass &gp) {
     a.st_begin = gp.st_begin;
     a.st_end = gp.st_end;
     a.area = gp.area;
+    a.mem_begin = gp.mem_begin;
+    a.mem_end = gp.mem_end;
     return a;
 }
 

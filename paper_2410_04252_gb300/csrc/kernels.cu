@@ -575,7 +575,7 @@ template <int OFF> __device__ __forceinline__ float2 lds_f2_off(uint32_t addr) {
 // (a thread bit just selects the phase or sign for all of its registers).
 // One shared-memory transpose per phase instead of one barrier per gate.
 __device__ __forceinline__ uint32_t swz_tile(uint32_t i) {
-    return i ^ (((i >> 4) ^ (i >> 8)) & 15u);   // bijection; spreads strided lanes over the banks
+    return swz_slot(i);   // bijection; spreads strided lanes over the banks
 }
 
 template <typename R, int V, int B>
@@ -833,6 +833,19 @@ __device__ __forceinline__ void phase_index(uint32_t rmask, int k, uint32_t &bas
     for (int v = 1; v < (1 << RB); ++v) sp[v] = sp[v & (v - 1)] | rb[__ffs(v) - 1];
 }
 
+// The thread's tile bits outside rmask when the lane bits of the thread
+// index hold the tile bits in `lanes` (ascending) and the other thread index
+// bits hold the remaining non-register bits (ascending).
+__device__ __forceinline__ uint32_t phase_base(uint32_t rmask, uint32_t lanes, int k) {
+    const uint32_t all = (k >= 32) ? 0xFFFFFFFFu : ((1u << k) - 1u);
+    uint32_t base = 0, t = threadIdx.x;
+    for (uint32_t m = lanes; m; m &= m - 1, t >>= 1)
+        if (t & 1u) base |= m & (0u - m);
+    for (uint32_t m = all & ~rmask & ~lanes; m; m &= m - 1, t >>= 1)
+        if (t & 1u) base |= m & (0u - m);
+    return base;
+}
+
 // ---- register-blocked pass execution ----------------------------------
 // Complex64 amplitudes stay in one 64-bit register pair (re, im) while a
 // phase is in registers, so that rotations with real coefficients are pure
@@ -919,6 +932,26 @@ __device__ __forceinline__ R ra_ry_grad(const RA<R> *p, const RA<R> *l) {
             g += (l[w].x * p[v].x + l[w].y * p[v].y) - (l[v].x * p[w].x + l[v].y * p[w].y);
         }
         return g;
+    }
+}
+
+// sb[b] = sum_v (-1)^{bit b of v} tv[v] for every register bit b, by
+// halving: pair sums feed the next bit, pair differences sum into sb[b].
+template <typename R, int RB>
+__device__ __forceinline__ void signed_bit_sums(const R *tv, R *sb) {
+    constexpr int V = 1 << RB;
+    R cur[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) cur[v] = tv[v];
+#pragma unroll
+    for (int b = 0, n = V; b < RB; ++b, n >>= 1) {
+        R d = 0;
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) {
+            d += cur[2 * k] - cur[2 * k + 1];
+            cur[k] = cur[2 * k] + cur[2 * k + 1];
+        }
+        sb[b] = d;
     }
 }
 
@@ -1109,7 +1142,7 @@ __device__ __forceinline__ void load_tile_async(E *tile, const Cx<R> *psi, uint6
 // Shared-memory layout of a register-blocked pass (both kernels): the tiles,
 // then these tables (offsets in bytes from the end of the tiles).
 struct RegLayout {
-    uint32_t hioff, cs, steps, blocks, pbase, prb, acc, area, total;
+    uint32_t hioff, cs, steps, blocks, mem, pbase, prb, acc, area, total;
 };
 __host__ __device__ inline uint32_t align16u(uint32_t v) { return (v + 15u) & ~15u; }
 __host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, bool adj) {
@@ -1121,6 +1154,7 @@ __host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, 
     L.cs = o;    o = align16u(o + (uint32_t)amp * nops);
     L.steps = o; o = align16u(o + 16u * nst);
     L.blocks = o; o = align16u(o + (uint32_t)sizeof(DiagBlock) * nb);
+    L.mem = o;   o = align16u(o + (uint32_t)sizeof(DiagMember) * (uint32_t)(a.mem_end - a.mem_begin));
     L.pbase = o; o = align16u(o + 2u * kRegThreads * nph);
     L.prb = o;   o = align16u(o + 8u * nph);
     L.acc = o;   o = align16u(o + (adj ? 8u * (kRegThreads / 32) * nops : 0u));
@@ -1154,10 +1188,11 @@ __device__ void reg_setup(unsigned char *sm, const RegLayout &L, const GatePassA
     }
     for (int s = a.st_begin + tid; s < a.st_end; s += NT) st[s - a.st_begin] = steps[s];
     for (int b = a.db_begin + tid; b < a.db_end; b += NT) bl[b - a.db_begin] = dblocks[b];
+    DiagMember *mem = reinterpret_cast<DiagMember *>(sm + L.mem);
+    for (int m = a.mem_begin + tid; m < a.mem_end; m += NT) mem[m - a.mem_begin] = dmem[m];
     for (int ph = a.ph_begin; ph < a.ph_end; ++ph) {
         const uint32_t rmask = phases[ph].rmask;
-        uint32_t base, sp[V];
-        phase_index<RB>(rmask, a.k, base, sp);
+        const uint32_t base = phase_base(rmask, phases[ph].lanes, a.k);
         pbase[(ph - a.ph_begin) * NT + tid] = (uint16_t)base;
         if (tid < 4) {
             uint32_t rm = rmask, bitv = 0;
@@ -1171,8 +1206,7 @@ __device__ void reg_setup(unsigned char *sm, const RegLayout &L, const GatePassA
     unsigned char *area = sm + L.area;
     for (int b = a.db_begin; b < a.db_end; ++b) {
         const DiagBlock B = dblocks[b];
-        uint32_t base, sp[V];
-        phase_index<RB>(B.rmask, a.k, base, sp);
+        const uint32_t base = phase_base(B.rmask, B.lanes, a.k);
         if (B.kind == 0) {
             Cx<R> *tab = reinterpret_cast<Cx<R> *>(area + B.smem);
             uint8_t *zmv = area + B.smem + V * V * (int)sizeof(Cx<R>);
@@ -1354,6 +1388,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const uint16_t *pbase = reinterpret_cast<const uint16_t *>(sm + L.pbase);
     const uint16_t *prb = reinterpret_cast<const uint16_t *>(sm + L.prb);
     const unsigned char *area = sm + L.area;
+    const DiagMember *mem = reinterpret_cast<const DiagMember *>(sm + L.mem);
     const uint64_t ntiles = 1ull << a.nout;
     const uint32_t lowmask = (1u << a.nlow) - 1u;
     const uint64_t mine = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -1437,16 +1472,10 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     }
                     if (B.kind == 0) {
                         R sb[4] = {0, 0, 0, 0};
-#pragma unroll
-                        for (int b = 0; b < RB; ++b) {
-                            R acc_b = 0;
-#pragma unroll
-                            for (int v = 0; v < V; ++v) acc_b += ((v >> b) & 1) ? -tv[v] : tv[v];
-                            sb[b] = acc_b;
-                        }
+                        signed_bit_sums<R, RB>(tv, sb);
                         const R red = warp_sum4<R>(sb[0], sb[1], sb[2], sb[3]);
                         for (int mi = B.m_begin; mi < B.m_end; ++mi) {
-                            const DiagMember m = dmem[mi];
+                            const DiagMember m = mem[mi - a.mem_begin];
                             if (m.type == SV_DM_REG_RZ && lane == 8 * m.a)
                                 acc[(m.op - a.op_begin) * nwarps + warp] += (double)red;
                         }
@@ -1457,11 +1486,13 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                             int opi[4] = {-1, -1, -1, -1};
 #pragma unroll
                             for (int j = 0; j < 4; ++j) {
-                                if (m0 + j >= B.m_end) break;
-                                const DiagMember m = dmem[m0 + j];
-                                if (m.type != SV_DM_THR_RZ) continue;
-                                vals[j] = ((base >> m.a) & 1u) ? -tot : tot;
-                                opi[j] = m.op - a.op_begin;
+                                if (m0 + j < B.m_end) {
+                                    const DiagMember m = mem[m0 + j - a.mem_begin];
+                                    if (m.type == SV_DM_THR_RZ) {
+                                        vals[j] = ((base >> m.a) & 1u) ? -tot : tot;
+                                        opi[j] = m.op - a.op_begin;
+                                    }
+                                }
                             }
                             const R red = warp_sum4<R>(vals[0], vals[1], vals[2], vals[3]);
 #pragma unroll
@@ -1481,6 +1512,8 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     }
                 }
             }
+            // the slots again (fewer registers live across the steps)
+            phase_slots<RB>(idx, pbase[(ph - a.ph_begin) * NT + threadIdx.x], prb + (ph - a.ph_begin) * 4);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 tp[idx[v]] = xp[v];

@@ -17,6 +17,7 @@ struct GatePassArgs {
     int db_begin, db_end;    // diagonal blocks of the pass
     int st_begin, st_end;    // steps of the pass's register phases
     int area;                // bytes of the diagonal-block data
+    int mem_begin, mem_end;  // diagonal-block members of the pass
     int8_t hi[40];
     int8_t out[64];
 };

@@ -450,6 +450,36 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, in
 // targets (C1 is kept).  The pass's ops are reordered phase by phase.
 bool diag_kind(int kind) { return kind == SV_RZ || kind == SV_CZ; }
 
+// Lane bits of a phase: the 5 tile bits outside the register set that the
+// lane bits of the thread index hold.  A warp gathers its 32 x 2^r
+// amplitudes by shared-memory slot swz_slot(base | v); for 8-byte (and
+// 16-byte) elements it takes no extra bank wavefront when the lanes' slots
+// differ in all 4 low bits, i.e. when the low-4-bit parts of the lane bits'
+// slots have rank 4.  The lanes are picked greedily (lowest bits first) for
+// that rank, then padded with the lowest remaining bits; the other thread
+// index bits take the remaining bits in ascending order.
+uint32_t phase_lanes(uint32_t rmask, int k) {
+    uint32_t lanes = 0, span[4] = {0, 0, 0, 0};
+    int rank = 0, nl = 0;
+    for (int t = 0; t < k && nl < 5 && rank < 4; ++t) {
+        if (rmask >> t & 1u) continue;
+        uint32_t v = swz_slot(1u << t) & 15u;
+        for (int i = 3; i >= 0; --i)
+            if ((v >> i & 1u) && span[i]) v ^= span[i];
+        if (!v) continue;
+        span[31 - __builtin_clz(v)] = v;
+        ++rank;
+        lanes |= 1u << t;
+        ++nl;
+    }
+    for (int t = 0; t < k && nl < 5; ++t)
+        if (!(rmask >> t & 1u) && !(lanes >> t & 1u)) {
+            lanes |= 1u << t;
+            ++nl;
+        }
+    return lanes;
+}
+
 void plan_phases(QsuPlan &P) {
     for (auto &gp : P.passes) {
         const int r = gp.k - 9;                       // 512 threads
@@ -485,6 +515,7 @@ void plan_phases(QsuPlan &P) {
             for (uint32_t fr = all & ~Rm; __builtin_popcount(Rm) < r && fr; fr &= fr - 1) Rm |= fr & (0u - fr);
             Phase ph;
             ph.rmask = Rm;
+            ph.lanes = phase_lanes(Rm, gp.k);
             ph.st_begin = ph.st_end = 0;
             ph.op_begin = gp.op_begin + (int32_t)out.size();
             uint32_t av = all;
@@ -634,7 +665,7 @@ void plan_steps(QsuPlan &P, int max_diag, int amp) {
                 B.rmask = F.rmask;
                 B.kind = kind;
                 B.smem = off;
-                B.pad = 0;
+                B.lanes = F.lanes;
                 for (size_t u = 0; u < ops.size(); ++u) {
                     P.dmembers.push_back(member(ops[u], (int)out.size()));
                     if (idx.empty()) emit_op(ops[u]);
@@ -707,6 +738,8 @@ void plan_steps(QsuPlan &P, int max_diag, int amp) {
         gp.st_begin = P.phases[gp.ph_begin].st_begin;
         gp.st_end = P.phases[gp.ph_end - 1].st_end;
         gp.area = area;
+        gp.mem_begin = gp.db_end > gp.db_begin ? P.dblocks[gp.db_begin].m_begin : 0;
+        gp.mem_end = gp.db_end > gp.db_begin ? P.dblocks[gp.db_end - 1].m_end : 0;
     }
 }
 

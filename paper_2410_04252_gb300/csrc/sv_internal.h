@@ -58,6 +58,7 @@ struct GatePass {
     int32_t db_begin = 0, db_end = 0;    // diagonal blocks of the pass (register-blocked passes)
     int32_t st_begin = 0, st_end = 0;    // steps of the pass's phases
     int32_t area = 0;                    // bytes of the pass's diagonal-block data (shared memory)
+    int32_t mem_begin = 0, mem_end = 0;  // the pass's diagonal-block members (QsuPlan::dmembers)
 };
 
 // A run of consecutive diagonal operations (RZ, CZ) inside one register
@@ -76,7 +77,8 @@ struct DiagBlock {
     int32_t m_begin, m_end;       // into QsuPlan::dmembers
     uint32_t rmask;               // register tile bits of the phase
     int32_t kind;                 // 0 register block, 1 thread block
-    int32_t smem, pad;
+    int32_t smem;
+    uint32_t lanes;               // the phase's lane bits (Phase::lanes)
 };
 enum { SV_DM_REG_RZ = 0, SV_DM_THR_RZ = 1, SV_DM_REG_CZ = 2, SV_DM_THR_CZ = 3, SV_DM_MIX_CZ = 4 };
 struct DiagMember {
@@ -95,6 +97,7 @@ struct Phase {
     uint32_t rmask;
     int32_t op_begin, op_end;
     int32_t st_begin, st_end;   // steps of the phase (QsuPlan::steps)
+    uint32_t lanes;             // tile bits held by the lane bits of the thread index (phase_lanes)
 };
 
 // A step of a register phase, executed as one unit by the register-blocked
@@ -103,6 +106,15 @@ struct Phase {
 // DIAG: a diagonal block (a = its index in QsuPlan::dblocks), ops = its
 // members.  OP: one operation (a = op_begin), applied by the generic code.
 enum { SV_STEP_ROT = 0, SV_STEP_DIAG = 1, SV_STEP_OP = 2 };
+// The shared-memory slot of tile index i in the register-blocked passes: a
+// linear (XOR) swizzle of the low 4 bits by bits 4..11, so that slot(a | b)
+// = slot(a) ^ slot(b) for disjoint a, b.
+#ifdef __CUDACC__
+#define SV_HD __host__ __device__
+#else
+#define SV_HD
+#endif
+SV_HD inline uint32_t swz_slot(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15u); }
 // Shared memory of a register-blocked pass of k staged bits (512 threads,
 // amplitudes of amp bytes): the block area needs at most this much beyond
 // the tiles, tables and accumulators, and each block takes
@@ -117,7 +129,7 @@ inline int reg_pass_fixed_bytes(int k, int nlow, int nops, int nsteps, int nphas
     // steps, block headers, per-phase thread bases and register offsets,
     // FP64 per-warp gradient slots, alignment
     return 2 * (1 << k) * amp + 8 * (1 << (k - nlow)) + nops * amp + 16 * nsteps + 32 * kMaxPassDiag +
-           nphases * (2 * kRegThreads + 8) + nops * (kRegThreads / 32) * 8 + 256;
+           16 * nops + nphases * (2 * kRegThreads + 8) + nops * (kRegThreads / 32) * 8 + 256;
 }
 struct RegStep {
     int32_t type, a;
