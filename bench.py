@@ -51,7 +51,10 @@ def parse():
     ap.add_argument("--no-direct", action="store_true")
     ap.add_argument("--plan-table", action="store_true", help="print plan-level QR counts (host only) and exit")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default options")
-    ap.add_argument("--cpu-n", type=int, default=22, help="oracle sample size (qubits)")
+    ap.add_argument("--cpu-n", type=int, default=22, help="qubits of the measured same-size oracle baseline")
+    ap.add_argument("--ref-n", type=int, default=20, help="qubits of the reference arm's per-step oracle sample")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the headline workload (no further configs in the line)")
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--low-bits", type=int, default=0)
     ap.add_argument("--evc-low-bits", type=int, default=0)
@@ -197,7 +200,33 @@ def omp_threads():
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
+def oracle_step(cfg_id, n_s):
+    """One real step of the oracle's own path at n_s qubits (QSU gate by
+    gate, then EVC of every string; for the batched workload one state of the
+    mean depth): wall ms and a description."""
+    import oracle
+    from paper_2410_04252_gb300 import workloads as W
+    cfg = W.CONFIGS[cfg_id]
+    layers = (cfg["layers"] + cfg["min_layers"]) // 2 if cfg.get("batch", 1) > 1 else cfg["layers"]
+    circ = W.make_circuit(cfg, n_s, layers)
+    params = W.make_params(cfg_id, circ)
+    ham = W.make_hamiltonian(cfg_id, n_s)
+    t0 = time.perf_counter()
+    psi = oracle.apply_circuit(oracle.basis_state(n_s, W.make_init(cfg, n_s)), circ, params)
+    if ham is not None:
+        oracle.energy(psi, ham)
+    ms = (time.perf_counter() - t0) * 1e3
+    what = ("oracle FP64 QSU (%d gates) + EVC of all %d strings of the workload at n=%d (no gradient)"
+            % (circ.m, len(ham.coeffs) if ham is not None else 0, n_s))
+    return ms, what
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, timed for real on the
+    host cores, each step one run of the workload's QSU + EVC at --ref-n
+    qubits (a bounded sample of the workload: same ansatz, depth and
+    Hamiltonian, fewer qubits).  Its full-size estimate (scaled to n and with
+    the parameter-shift gradient) is reported beside, labelled as one."""
     rank, local, world = rank_info()
     if rank != 0:
         return 0
@@ -206,27 +235,29 @@ def run_reference(args):
     from paper_2410_04252_gb300 import workloads as W
     cfg = W.CONFIGS[args.config]
     n_full = args.n or cfg["n"]
-    n_s = min(args.cpu_n, n_full)
+    n_s = min(args.ref_n, n_full)
     for _ in range(args.warmup):
-        oracle_sample(args.config, n_full, min(n_s, 16))
-    vals, wall = [], []
+        oracle_step(args.config, min(n_s, 14))
+    vals = []
+    what = ""
     for _ in range(args.steps):
-        est, sample, w = oracle_sample(args.config, n_full, n_s)
-        vals.append(est)
-        wall.append(w)
+        ms, what = oracle_step(args.config, n_s)
+        vals.append(ms)
     ms = statistics.median(vals)
+    est_ms, est_how, _ = oracle_sample(args.config, n_full, n_s)
     metric, value, unit, hib = METRIC, ms, "ms", False
     if cfg["work"] == "batch":
         metric = BATCH_METRIC
-        value, unit, hib = cfg["batch"] / (ms * 1e-3), "states/s", True
+        value, unit, hib = 1.0 / (ms * 1e-3), "states/s", True
     line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "n": n_full, "g": cfg["g"], "nterms": cfg["nterms"]},
+            "config": {"workload": cfg["name"], "n": n_s, "n_workload": n_full, "g": cfg["g"],
+                       "nterms": cfg["nterms"], "sample": what},
             "cpu_baseline": {"value": value, "unit": unit, "cores": omp_threads(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": what + " (measured, median of the timed steps)"},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "sample_wall_s": statistics.median(wall)}
+            "estimate_full_workload_ms": est_ms, "estimate_how": est_how}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -247,6 +278,237 @@ def reduce_times(dev_ms, wall_ms, steps, world, dist=None, device="cpu"):
     return dev_ms, wall_ms, dev_ms / steps, steps * world / (dev_ms * 1e-3), wall_ms / steps
 
 
+def _timed_region(fn, stream, clocks):
+    """Run fn() between CUDA events on `stream` (synchronised on both sides),
+    with nvidia-smi clocks sampled meanwhile.  Returns (device ms, wall ms,
+    clocks, fn's result)."""
+    import torch
+    torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    ev0.record(stream)
+    res = fn()
+    ev1.record(stream)
+    ev1.synchronize()
+    wall = (time.perf_counter() - w0) * 1e3
+    clk = clocks.stop() if clocks is not None else None
+    return ev0.elapsed_time(ev1), wall, clk, res
+
+
+class Workload:
+    """One workload (configuration, qubit count, dtype) on one handle: its
+    seeded inputs in pinned host memory and the step of its path through the
+    public API (reset, QSU, EVC and, for the gradient workload, lambda and
+    the reverse sweep)."""
+
+    def __init__(self, cfg_id, n=None, dtype=None, opt_args=None, work=None):
+        import numpy as np
+        import torch
+        from paper_2410_04252_gb300 import sv
+        from paper_2410_04252_gb300 import workloads as W
+        self.sv, self.np = sv, np
+        self.cfg_id = cfg_id
+        self.cfg = cfg = W.CONFIGS[cfg_id]
+        self.n = n or cfg["n"]
+        self.g = cfg["g"]
+        self.dtype = dtype if dtype is not None else (sv.C64 if cfg["dtype"] == "c64" else sv.C128)
+        self.work = work or cfg["work"]
+        self.circ = W.make_circuit(cfg, self.n)
+        ham = W.make_hamiltonian(cfg_id, self.n)
+        paulis, coeffs = sv.hamiltonian_arrays(ham) if ham is not None else (None, np.zeros(0))
+        # the step's host inputs live in pinned memory (copied to the device
+        # by every call through the public API)
+        self.params = torch.from_numpy(W.make_params(cfg_id, self.circ)).pin_memory().numpy()
+        self.coeffs = torch.from_numpy(np.ascontiguousarray(coeffs, np.float64)).pin_memory().numpy()
+        self.paulis = None
+        if paulis is not None:
+            self.paulis = torch.from_numpy(np.ascontiguousarray(paulis).view(np.int64)).pin_memory().numpy().view(
+                np.uint64)
+        self.init = W.make_init(cfg, self.n)
+        opt = sv.default_options(self.dtype)
+        a = opt_args
+        if a is not None:
+            if a.tile_bits:
+                opt.tile_bits = a.tile_bits
+            if a.low_bits:
+                opt.low_bits = a.low_bits
+            if a.evc_low_bits:
+                opt.evc_low_bits = a.evc_low_bits
+            if a.evc_span >= 0:
+                opt.evc_span = a.evc_span
+        opt.profile = 1
+        self.opt = opt
+        self.sim = sv.StateVector(self.n, self.g, self.dtype, options=opt)
+        if self.work == "qsu+evc+grad":
+            self.sim.ensure_lambda()
+
+    def step(self, schedule):
+        """One step; stats of all its calls merged into sim.last_stats.
+        Returns (energy, gradient)."""
+        sim, sv = self.sim, self.sv
+        if self.work == "qsu+evc+grad":
+            e, gr, _ = sim.vqe_step(self.init, self.circ, self.params, paulis=self.paulis, coeffs=self.coeffs,
+                                    schedule=schedule)
+            return e, gr
+        sim.reset(self.init)
+        st = sim.apply_circuit(self.circ, self.params, schedule)
+        e = 0.0
+        if self.work == "qsu+evc":
+            e, _ = sim.expect(paulis=self.paulis, coeffs=self.coeffs, schedule=schedule)
+            st = sv.merge_stats(st, sim.last_stats)
+        else:
+            sim.synchronize()
+        sim.last_stats = st
+        return e, self.np.zeros(0)
+
+    def bytes_io(self):
+        """Host->device and device->host bytes of one step through the API."""
+        h2d = 2 * self.params.nbytes + (self.coeffs.nbytes + self.paulis.nbytes if self.paulis is not None else 0)
+        d2h = 16 + (8 * self.params.size if self.work == "qsu+evc+grad" else 0)
+        return h2d, d2h
+
+    def close(self):
+        import torch
+        self.sim.close()
+        del self.sim
+        torch.cuda.empty_cache()
+
+
+def measure(wl, schedule, steps, warmup, clocks=None):
+    """Warm-up, then `steps` timed steps of one schedule: device and wall time
+    per step, per-kernel-kind launches / time / algorithmic bytes, counts."""
+    import torch
+    sv = wl.sv
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    for _ in range(warmup):
+        wl.step(schedule)
+    warm_s = time.perf_counter() - t0
+    agg = {k: [0, 0.0, 0.0] for k in sv.KERNEL_KINDS}
+    out = {}
+
+    def body():
+        launches = 0
+        e = gr = None
+        for _ in range(steps):
+            e, gr = wl.step(schedule)
+            st = wl.sim.last_stats
+            launches += st.launches
+            for i, k in enumerate(sv.KERNEL_KINDS):
+                agg[k][0] += st.kernels[i]
+                agg[k][1] += st.bytes[i]
+                agg[k][2] += st.ms[i]
+            out["counts"] = dict(qsu_tiles=st.qsu_tiles, qsu_qrs=st.qsu_qrs, qsu_passes=st.qsu_passes,
+                                 evc_tiles=st.evc_tiles, evc_qrs=st.evc_qrs, evc_passes=st.evc_passes,
+                                 hpsi_passes=st.hpsi_passes, adj_passes=st.adj_passes)
+        return launches, e, gr
+
+    dev_ms, wall_ms, clk, (launches, e, gr) = _timed_region(body, stream, clocks)
+    out.update(dev_ms=dev_ms, wall_ms=wall_ms, clocks=clk, launches=launches, energy=e, grad=gr, agg=agg,
+               warm_s=warm_s, steps=steps, warmup=warmup)
+    return out
+
+
+def kernel_table(agg, steps, peak, peak_src):
+    """Per-kind summary and the dominant kind's roofline entry."""
+    kinds = {}
+    total = max(sum(v[2] for v in agg.values()), 1e-9)
+    for k, (cnt, byts, ms) in agg.items():
+        if cnt:
+            kinds[k] = {"launches_per_step": cnt / steps, "ms_per_step": ms / steps, "share": ms / total,
+                        "algorithmic_GBps": (byts / (ms * 1e-3) / 1e9) if ms > 0 and byts > 0 else None,
+                        "bytes_per_launch": byts / cnt,
+                        "frac_of_measured_hbm": ((byts / (ms * 1e-3) / 1e9) / peak) if ms > 0 and byts > 0 else None}
+    dom = max((k for k in kinds if agg[k][1] > 0), key=lambda k: agg[k][2])
+    cnt, byts, ms = agg[dom]
+    achieved = byts / (ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dom, byts / cnt)}
+    return kinds, roof
+
+
+def other_schedule(wl, schedule, steps, warmup, ref):
+    """The same step under another schedule: time per step, QR counts and the
+    energy (and gradient) difference from the lazy step."""
+    import numpy as np
+    m = measure(wl, schedule, steps, warmup)
+    c = m["counts"]
+    d = {"ms_per_step": m["dev_ms"] / steps, "qsu_qrs": c["qsu_qrs"], "evc_qrs": c["evc_qrs"],
+         "qsu_passes": c["qsu_passes"], "evc_passes": c["evc_passes"], "steps": steps, "warmup": warmup,
+         "energy_diff_vs_lazy": abs(m["energy"] - ref["energy"])}
+    if m["grad"] is not None and m["grad"].size:
+        d["grad_maxdiff_vs_lazy"] = float(np.max(np.abs(m["grad"] - ref["grad"])))
+    return d
+
+
+def extra_workload(cfg_id, steps, warmup, peak, peak_src, local, dtype=None, eager=True):
+    """A further workload of the benchmark (a BASELINE config) on this GPU:
+    its own timed region, clocks, roofline of its dominant kernel, end-to-end
+    time and, for QSU / EVC workloads, the eager schedule beside it."""
+    from paper_2410_04252_gb300 import sv
+    wl = Workload(cfg_id, dtype=dtype)
+    try:
+        m = measure(wl, sv.LAZY, steps, warmup, ClockSampler(local))
+        kinds, roof = kernel_table(m["agg"], steps, peak, peak_src)
+        h2d, d2h = wl.bytes_io()
+        state_gb = (1 << wl.n) * (8 if wl.dtype == sv.C64 else 16) / 1e9
+        d = {"workload": wl.cfg["name"] if dtype is None else wl.cfg["name"].replace("c64", "c128"),
+             "metric": METRIC, "value": m["dev_ms"] / steps, "unit": "ms", "ms_per_step": m["dev_ms"] / steps,
+             "higher_is_better": False, "steps": steps, "warmup": warmup,
+             "dtype": "c64 (f32 math, f64 accumulation)" if wl.dtype == sv.C64 else "c128 (f64)",
+             "config": {"n": wl.n, "g": wl.g, "gates": wl.circ.m, "params": wl.circ.nparams,
+                        "nterms": len(wl.coeffs), "work": wl.work, "schedule": "lazy", "state_GB": state_gb,
+                        "l2": "inputs larger than L2 (state %.1f GB)" % state_gb},
+             "roofline": roof, "kernels": kinds, "counts": m["counts"], "clocks": m["clocks"],
+             "gpu_launches": m["launches"], "energy": m["energy"],
+             "e2e": {"value": m["wall_ms"] / steps, "unit": "ms", "h2d_bytes_per_step": h2d,
+                     "d2h_bytes_per_step": d2h, "how": "wall clock around the public calls of the step"}}
+        if eager:
+            d["eager"] = other_schedule(wl, sv.EAGER, 1, 1, m)
+            d["eager"]["speedup_lazy_over_eager"] = d["eager"]["ms_per_step"] / d["ms_per_step"]
+        return d
+    finally:
+        wl.close()
+
+
+def same_n_baseline(cfg_id, n_s, args):
+    """The oracle timed for real on the host cores at a size it finishes in
+    seconds (QSU gate by gate + the full Hamiltonian string by string, FP64),
+    beside the library at the same size: its whole step and its QSU + EVC
+    alone (the oracle's work), both device-timed."""
+    import oracle
+    from paper_2410_04252_gb300 import sv
+    from paper_2410_04252_gb300 import workloads as W
+    oracle.build()
+    cfg = W.CONFIGS[cfg_id]
+    circ = W.make_circuit(cfg, n_s)
+    params = W.make_params(cfg_id, circ)
+    ham = W.make_hamiltonian(cfg_id, n_s)
+    t0 = time.perf_counter()
+    psi = oracle.apply_circuit(oracle.basis_state(n_s, W.make_init(cfg, n_s)), circ, params)
+    t1 = time.perf_counter()
+    e_orc = oracle.energy(psi, ham) if ham is not None else 0.0
+    t2 = time.perf_counter()
+    out = {"n": n_s, "cores": omp_threads(), "oracle_qsu_ms": (t1 - t0) * 1e3, "oracle_evc_ms": (t2 - t1) * 1e3,
+           "measured_ms": (t2 - t0) * 1e3, "oracle_energy": e_orc,
+           "what": "oracle FP64 QSU (%d gates) + EVC of all %d strings at n=%d, no gradient"
+                   % (circ.m, len(ham.coeffs) if ham is not None else 0, n_s)}
+    for work, key in (("qsu+evc", "gpu_same_n_qsu_evc_ms"), (cfg["work"], "gpu_same_n_step_ms")):
+        wl = Workload(cfg_id, n=n_s, work=work)
+        try:
+            m = measure(wl, sv.LAZY, 5, 3)
+            out[key] = m["dev_ms"] / 5
+            if work == "qsu+evc":
+                out["gpu_energy_diff_vs_oracle"] = abs(m["energy"] - e_orc)
+        finally:
+            wl.close()
+    out["speedup_same_n_qsu_evc"] = out["measured_ms"] / out["gpu_same_n_qsu_evc_ms"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -257,168 +519,45 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2410_04252_gb300 import sv
-    from paper_2410_04252_gb300 import workloads as W
 
-    cfg = W.CONFIGS[args.config]
-    n = args.n or cfg["n"]
-    g = cfg["g"]
-    dtype = sv.C64 if cfg["dtype"] == "c64" else sv.C128
-    circ = W.make_circuit(cfg, n)
-    ham = W.make_hamiltonian(args.config, n)
-    paulis, coeffs = sv.hamiltonian_arrays(ham) if ham is not None else (None, np.zeros(0))
-    # the step's host inputs live in pinned memory (copied to the device by
-    # every call through the public API)
-    params = torch.from_numpy(W.make_params(args.config, circ)).pin_memory().numpy()
-    coeffs = torch.from_numpy(np.ascontiguousarray(coeffs, np.float64)).pin_memory().numpy()
-    if paulis is not None:
-        paulis = torch.from_numpy(np.ascontiguousarray(paulis).view(np.int64)).pin_memory().numpy().view(np.uint64)
-    init = W.make_init(cfg, n)
-    opt = sv.default_options(dtype)
-    if args.tile_bits:
-        opt.tile_bits = args.tile_bits
-    if args.low_bits:
-        opt.low_bits = args.low_bits
-    if args.evc_low_bits:
-        opt.evc_low_bits = args.evc_low_bits
-    if args.evc_span >= 0:
-        opt.evc_span = args.evc_span
-    opt.profile = 1
-    sim = sv.StateVector(n, g, dtype, options=opt)
-    sim.ensure_lambda()
-    stream = torch.cuda.current_stream()
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    work = cfg["work"]
-
-    def step(schedule):
-        """One step of the workload's path; stats of all its calls merged
-        into sim.last_stats.  Returns (energy, gradient)."""
-        if work == "qsu+evc+grad":
-            e, gr, _ = sim.vqe_step(init, circ, params, paulis=paulis, coeffs=coeffs, schedule=schedule)
-            return e, gr
-        sim.reset(init)
-        st = sim.apply_circuit(circ, params, schedule)
-        e = 0.0
-        if work == "qsu+evc":
-            e, _ = sim.expect(paulis=paulis, coeffs=coeffs, schedule=schedule)
-            st = sv.merge_stats(st, sim.last_stats)
-        else:
-            sim.synchronize()
-        sim.last_stats = st
-        return e, np.zeros(0)
-
+    peak, peak_src = measured_peaks()
+    wl = Workload(args.config, n=args.n or None, opt_args=args)
+    n, g, dtype, opt = wl.n, wl.g, wl.dtype, wl.opt
     t_setup = time.perf_counter()
     for _ in range(args.warmup):
-        e, gr = step(sv.LAZY)
+        wl.step(sv.LAZY)
     plan_s = time.perf_counter() - t_setup
-
-    clocks = ClockSampler(local)
-    barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    w0 = time.perf_counter()
-    ev0.record(stream)
-    agg = {k: [0, 0.0, 0.0] for k in sv.KERNEL_KINDS}
-    launches = 0
-    counts = {}
-    for _ in range(args.steps):
-        e, gr = step(sv.LAZY)
-        st = sim.last_stats
-        launches += st.launches
-        for i, k in enumerate(sv.KERNEL_KINDS):
-            agg[k][0] += st.kernels[i]
-            agg[k][1] += st.bytes[i]
-            agg[k][2] += st.ms[i]
-        counts = dict(qsu_tiles=st.qsu_tiles, qsu_qrs=st.qsu_qrs, qsu_passes=st.qsu_passes,
-                      evc_tiles=st.evc_tiles, evc_qrs=st.evc_qrs, evc_passes=st.evc_passes,
-                      hpsi_passes=st.hpsi_passes, adj_passes=st.adj_passes)
-    ev1.record(stream)
-    ev1.synchronize()
-    wall_ms = (time.perf_counter() - w0) * 1e3
-    barrier()
-    clk = clocks.stop()
-    dev_ms, wall_ms, ms_per_step, job_iters_per_s, e2e_value = reduce_times(ev0.elapsed_time(ev1), wall_ms,
-                                                                             args.steps, world, dist, "cuda")
+    if dist is not None:
+        dist.barrier()
+    m = measure(wl, sv.LAZY, args.steps, 0, ClockSampler(local))
+    if dist is not None:
+        dist.barrier()
+    dev_ms, wall_ms, ms_per_step, job_iters_per_s, e2e_value = reduce_times(m["dev_ms"], m["wall_ms"], args.steps,
+                                                                             world, dist, "cuda")
     value = ms_per_step
-
-    # eager schedule on the same GPU (shorter run)
-    eager = None
+    eager = direct = hier = ldiag = None
     if not args.no_eager:
-        for _ in range(args.eager_warmup):
-            step(sv.EAGER)
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        est = None
-        for _ in range(args.eager_steps):
-            ee, eg = step(sv.EAGER)
-            est = sim.last_stats
-        a1.record(stream)
-        a1.synchronize()
-        eager_ms = a0.elapsed_time(a1) / max(args.eager_steps, 1)
-        eager = {"ms_per_step": eager_ms, "speedup_lazy_over_eager": eager_ms / ms_per_step,
-                 "qsu_qrs": est.qsu_qrs, "evc_qrs": est.evc_qrs, "qsu_passes": est.qsu_passes,
-                 "evc_passes": est.evc_passes, "steps": args.eager_steps, "warmup": args.eager_warmup,
-                 "energy_diff_vs_lazy": abs(ee - e),
-                 "grad_maxdiff_vs_lazy": float(np.max(np.abs(eg - gr))) if gr.size else None}
-
-    # no virtual-chunk constraint (not the paper's method): the single-GPU optimum
-    direct = None
+        eager = other_schedule(wl, sv.EAGER, args.eager_steps, args.eager_warmup, m)
+        eager["speedup_lazy_over_eager"] = eager["ms_per_step"] / ms_per_step
     if not args.no_direct:
-        step(sv.DIRECT)
-        torch.cuda.synchronize()
-        d0 = torch.cuda.Event(enable_timing=True)
-        d1 = torch.cuda.Event(enable_timing=True)
-        d0.record(stream)
-        de, dg = step(sv.DIRECT)
-        dst = sim.last_stats
-        d1.record(stream)
-        d1.synchronize()
-        dms = d0.elapsed_time(d1)
-        direct = {"ms_per_step": dms, "lazy_over_direct": ms_per_step / dms, "qsu_qrs": dst.qsu_qrs,
-                  "evc_qrs": dst.evc_qrs, "evc_passes": dst.evc_passes, "energy_diff_vs_lazy": abs(de - e)}
-
-    # hierarchical tiling (Alg. 4/5, 8 chunks per node) on the same GPU
-    hier = None
-    if not args.no_direct and g >= 3:
-        ho = sim.options()
-        ho.intra_bits = 3
-        sim.set_options(ho)
-        step(sv.HIER)
-        torch.cuda.synchronize()
-        h0 = torch.cuda.Event(enable_timing=True)
-        h1 = torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        he, hg = step(sv.HIER)
-        hst = sim.last_stats
-        h1.record(stream)
-        h1.synchronize()
-        hms = h0.elapsed_time(h1)
-        hier = {"ms_per_step": hms, "intra_bits": 3, "qsu_qrs": hst.qsu_qrs, "evc_qrs": hst.evc_qrs,
-                "energy_diff_vs_lazy": abs(he - e)}
-        ho.intra_bits = 0
-        sim.set_options(ho)
-
-    # diagonal gates exempt from locality (not the paper's method)
-    ldiag = None
-    if not args.no_direct:
-        step(sv.LAZY_DIAG)
-        torch.cuda.synchronize()
-        x0 = torch.cuda.Event(enable_timing=True)
-        x1 = torch.cuda.Event(enable_timing=True)
-        x0.record(stream)
-        xe, xg = step(sv.LAZY_DIAG)
-        xst = sim.last_stats
-        x1.record(stream)
-        x1.synchronize()
-        ldiag = {"ms_per_step": x0.elapsed_time(x1), "qsu_qrs": xst.qsu_qrs, "evc_qrs": xst.evc_qrs,
-                 "energy_diff_vs_lazy": abs(xe - e)}
+        # no virtual-chunk constraint (not the paper's method): the single-GPU optimum
+        direct = other_schedule(wl, sv.DIRECT, 1, 1, m)
+        direct["lazy_over_direct"] = ms_per_step / direct["ms_per_step"]
+        if g >= 3:
+            # hierarchical tiling (Alg. 4/5, 8 chunks per node) on the same GPU
+            ho = wl.sim.options()
+            ho.intra_bits = 3
+            wl.sim.set_options(ho)
+            hier = other_schedule(wl, sv.HIER, 1, 1, m)
+            hier["intra_bits"] = 3
+            ho.intra_bits = 0
+            wl.sim.set_options(ho)
+        # diagonal gates exempt from locality (not the paper's method)
+        ldiag = other_schedule(wl, sv.LAZY_DIAG, 1, 1, m)
+    e, gr = m["energy"], m["grad"]
+    h2d, d2h = wl.bytes_io()
+    cfg, circ, coeffs = wl.cfg, wl.circ, wl.coeffs
+    wl.close()
 
     if rank != 0:
         if dist is not None:
@@ -426,25 +565,24 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    peak, peak_src = measured_peaks()
-    kinds = {}
-    for k, (cnt, byts, ms) in agg.items():
-        if cnt:
-            kinds[k] = {"launches_per_step": cnt / args.steps, "ms_per_step": ms / args.steps,
-                        "share": ms / max(sum(v[2] for v in agg.values()), 1e-9),
-                        "algorithmic_GBps": (byts / (ms * 1e-3) / 1e9) if ms > 0 and byts > 0 else None,
-                        "bytes_per_launch": byts / cnt}
-    dom = max((k for k in kinds if agg[k][1] > 0), key=lambda k: agg[k][2])
-    cnt, byts, ms = agg[dom]
-    achieved = byts / (ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom, byts / cnt)
-    h2d = 2 * params.nbytes
-    d2h = 16 + gr.nbytes
-
+    kinds, roof = kernel_table(m["agg"], args.steps, peak, peak_src)
     cpu = None
     if not args.no_cpu:
-        est_ms, sample, _ = oracle_sample(args.config, n, min(args.cpu_n, n))
-        cpu = {"value": est_ms, "unit": "ms", "cores": omp_threads(), "kind": "oracle", "sample": sample}
+        n_s = min(args.cpu_n, n)
+        same = same_n_baseline(args.config, n_s, args)
+        est_ms, sample, _ = oracle_sample(args.config, n, min(n_s, 22))
+        cpu = {"value": same["measured_ms"], "unit": "ms", "cores": same["cores"], "kind": "oracle",
+               "sample": same["what"] + " (measured); the same size on this GPU: gpu_same_n_qsu_evc_ms for the "
+                                        "same work, gpu_same_n_step_ms for the whole step",
+               "measured_ms": same["measured_ms"], "n": n_s, "same_n": same,
+               "estimate_full_step_ms": est_ms, "estimate_how": sample}
+
+    extras = {}
+    if args.config == 3 and not args.n and not args.headline_only and world == 1:
+        for cid in (1, 2):
+            extras["cfg%d" % cid] = extra_workload(cid, 3, 2, peak, peak_src, local)
+        extras["cfg4"] = run_batch(args, emit=False)
+        extras["cfg3_c128"] = extra_workload(3, 2, 1, peak, peak_src, local, dtype=sv.C128, eager=False)
 
     state_gb = (1 << n) * (8 if dtype == sv.C64 else 16) / 1e9
     line = {
@@ -458,27 +596,27 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "tile_bits": opt.tile_bits, "low_bits": opt.low_bits, "evc_low_bits": opt.evc_low_bits,
                    "evc_span": opt.evc_span},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "how": {"qsu+evc+grad": "wall clock around the public vqe_step call (host params/Hamiltonian in, "
                                "energy+grad out)",
                         "qsu+evc": "wall clock around reset + apply_circuit + expect (host params/Hamiltonian "
                                    "in, energy out)",
-                        "qsu": "wall clock around reset + apply_circuit + synchronize (host params in)"}[work]},
-        "gpu_launches": launches,
+                        "qsu": "wall clock around reset + apply_circuit + synchronize (host params in)"}[cfg["work"]]},
+        "gpu_launches": m["launches"],
         "replicas": {"n": world, "iterations_per_s": job_iters_per_s,
                      "how": "every rank runs its own replica; value is one replica's time per iteration"},
-        "clocks": clk,
+        "clocks": m["clocks"],
         "kernels": kinds,
-        "counts": counts,
+        "counts": m["counts"],
         "eager": eager,
         "direct": direct,
         "hier": hier,
         "lazy_diag": ldiag,
         "energy": e,
         "plan_and_warmup_s": plan_s,
+        "configs": extras or None,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -487,7 +625,7 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched workload: 256 independent n=18 states, HEA of 2..8 layers with
     per-state parameters, one shared 512-string random Hamiltonian; QSU,
     lambda/energy and adjoint gradient of every state in one persistent
@@ -563,6 +701,8 @@ def run_batch(args):
         "gpu_launches": st.launches * args.steps,
         "clocks": clk,
     }
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 

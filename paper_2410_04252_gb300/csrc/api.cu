@@ -1231,6 +1231,7 @@ sv_status sv_batch_run(int n, sv_dtype dt, int batch, const sv_gate *gates, cons
     const int hio = std::max(8, kmax - o.low_bits);
     PlanOptions po = plan_options(o);
     po.max_diag = 0;                     // the batched kernel applies RZ / CZ one by one
+    po.reg_pairs = false;                // and runs register phases of RY / RZ / CZ / 1-qubit matrices only
     std::vector<int32_t> l2p(n);
     for (int q = 0; q < n; ++q) l2p[q] = q;
     // one plan per distinct circuit

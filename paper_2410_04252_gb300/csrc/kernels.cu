@@ -955,6 +955,71 @@ __device__ __forceinline__ void signed_bit_sums(const R *tv, R *sb) {
     }
 }
 
+// Rotation (u, v) <- (c u - s v, s u + c v) of every register pair (u = x[v]
+// with (v & (MU | MV)) == MU, v' = v ^ MU ^ MV): RY on bit B is MU = 0,
+// MV = 1 << B; a Givens rotation MU = 1 << a, MV = 1 << b; the double
+// excitation MU, MV = the two bit pairs.
+template <typename R, int V, int MU, int MV>
+__device__ __forceinline__ void ra_pair_rot(RA<R> *x, const RotK<R> &k) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if ((v & (MU | MV)) != MU) continue;
+        const int w = v ^ MU ^ MV;
+        if constexpr (sizeof(R) == 4) {
+            unsigned long long t, uu, vv;
+            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(x[w]), "l"(k.NS));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(x[v]), "l"(k.C), "l"(t));
+            asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(x[w]), "l"(k.C));
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(x[v]), "l"(k.S), "l"(t));
+            x[v] = uu;
+            x[w] = vv;
+        } else {
+            const double2 a = x[v], b = x[w];
+            x[v] = make_double2(k.c * a.x - k.s * b.x, k.c * a.y - k.s * b.y);
+            x[w] = make_double2(k.s * a.x + k.c * b.x, k.s * a.y + k.c * b.y);
+        }
+    }
+}
+// Gradient part Im<lambda|G|psi> of such a rotation (G the subspace Y):
+// sum over the pairs of Re(conj(l_v') p_v) - Re(conj(l_v) p_v').
+template <typename R, int V, int MU, int MV>
+__device__ __forceinline__ R ra_pair_grad(const RA<R> *p, const RA<R> *l) {
+    R g = 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if ((v & (MU | MV)) != MU) continue;
+        const int w = v ^ MU ^ MV;
+        const Cx<R> pv = ra_cx<R>(p[v]), pw = ra_cx<R>(p[w]), lv = ra_cx<R>(l[v]), lw = ra_cx<R>(l[w]);
+        g += (lw.x * pv.x + lw.y * pv.y) - (lv.x * pw.x + lv.y * pw.y);
+    }
+    return g;
+}
+
+// Givens rotation on register bits (A, B), A holding the "1" of u; and the
+// double excitation on the four register bits with u's pair MU.
+#define SV_GIVENS_SWITCH(ra, rb, CALL)                                                       \
+    switch ((ra) * 4 + (rb)) {                                                               \
+    case 1: CALL(1, 2); break;   case 2: if constexpr (RB > 2) { CALL(1, 4); } break;        \
+    case 3: if constexpr (RB > 3) { CALL(1, 8); } break;                                     \
+    case 4: CALL(2, 1); break;   case 6: if constexpr (RB > 2) { CALL(2, 4); } break;        \
+    case 7: if constexpr (RB > 3) { CALL(2, 8); } break;                                     \
+    case 8: if constexpr (RB > 2) { CALL(4, 1); } break;                                     \
+    case 9: if constexpr (RB > 2) { CALL(4, 2); } break;                                     \
+    case 11: if constexpr (RB > 3) { CALL(4, 8); } break;                                    \
+    case 12: if constexpr (RB > 3) { CALL(8, 1); } break;                                    \
+    case 13: if constexpr (RB > 3) { CALL(8, 2); } break;                                    \
+    case 14: if constexpr (RB > 3) { CALL(8, 4); } break;                                    \
+    default: break;                                                                          \
+    }
+#define SV_DEXC_SWITCH(mu, CALL)                                                             \
+    if constexpr (RB == 4) {                                                                 \
+        switch (mu) {                                                                        \
+        case 3: CALL(3, 12); break;  case 5: CALL(5, 10); break;  case 6: CALL(6, 9); break; \
+        case 9: CALL(9, 6); break;   case 10: CALL(10, 5); break; case 12: CALL(12, 3); break; \
+        default: break;                                                                      \
+        }                                                                                    \
+    }
+
 // Four values reduced over a warp at once: lane L ends with the warp total
 // of value L >> 3 (6 shuffles instead of 20).
 template <typename R>
@@ -1018,6 +1083,22 @@ __device__ void ra_apply_op(RA<R> *x, DevOp op, uint32_t rmask, uint32_t base, C
         const Cx<R> *M = mats + op.mat;
 #define SV_C(B) ra_mat1<R, V, B>(x, M, adj)
         SV_RB_SWITCH(b0, SV_C)
+#undef SV_C
+        break;
+    }
+    case SV_GIVENS: {
+        const RotK<R> k = rotk<R>(cs.x, cs.y);
+        const int b1 = __popc(rmask & ((1u << op.t[1]) - 1u));
+#define SV_C(MU, MV) ra_pair_rot<R, V, MU, MV>(x, k)
+        SV_GIVENS_SWITCH(b0, b1, SV_C)
+#undef SV_C
+        break;
+    }
+    case SV_DEXC: {
+        const RotK<R> k = rotk<R>(cs.x, cs.y);
+        const int mu = (1 << b0) | (1 << __popc(rmask & ((1u << op.t[1]) - 1u)));
+#define SV_C(MU, MV) ra_pair_rot<R, V, MU, MV>(x, k)
+        SV_DEXC_SWITCH(mu, SV_C)
 #undef SV_C
         break;
     }
@@ -1101,6 +1182,16 @@ __device__ R ra_adjoint_op(RA<R> *p, RA<R> *l, DevOp op, uint32_t rmask, uint32_
     if (op.kind == SV_RY) {
 #define SV_C(B) g = ra_ry_grad<R, V, B>(p, l)
         SV_RB_SWITCH(b0, SV_C)
+#undef SV_C
+    } else if (op.kind == SV_GIVENS) {
+        const int b1 = __popc(rmask & ((1u << op.t[1]) - 1u));
+#define SV_C(MU, MV) g = ra_pair_grad<R, V, MU, MV>(p, l)
+        SV_GIVENS_SWITCH(b0, b1, SV_C)
+#undef SV_C
+    } else if (op.kind == SV_DEXC) {
+        const int mu = (1 << b0) | (1 << __popc(rmask & ((1u << op.t[1]) - 1u)));
+#define SV_C(MU, MV) g = ra_pair_grad<R, V, MU, MV>(p, l)
+        SV_DEXC_SWITCH(mu, SV_C)
 #undef SV_C
     } else if (op.kind == SV_RZ || op.kind == SV_OP_PHASE) {
         const bool reg = op.kind == SV_RZ && ((rmask >> t0) & 1u);

@@ -449,6 +449,9 @@ void plan_gate_passes(QsuPlan &P, const std::vector<Op> &ops, int k, int low, in
 // takes gates in order while they fit, a gate that does not fit blocking its
 // targets (C1 is kept).  The pass's ops are reordered phase by phase.
 bool diag_kind(int kind) { return kind == SV_RZ || kind == SV_CZ; }
+int op_qubits(int kind) {
+    return kind == SV_DEXC || kind == SV_MAT4 ? 4 : (kind == SV_CZ || kind == SV_GIVENS || kind == SV_MAT2) ? 2 : 1;
+}
 
 // Lane bits of a phase: the 5 tile bits outside the register set that the
 // lane bits of the thread index hold.  A warp gathers its 32 x 2^r
@@ -480,20 +483,23 @@ uint32_t phase_lanes(uint32_t rmask, int k) {
     return lanes;
 }
 
-void plan_phases(QsuPlan &P) {
+void plan_phases(QsuPlan &P, bool pairs) {
     for (auto &gp : P.passes) {
         const int r = gp.k - 9;                       // 512 threads
         if (r < 2) continue;
         bool ok = true;
         for (int o = gp.op_begin; o < gp.op_end; ++o) {
             const int kd = P.ops[o].kind;
-            if (kd != SV_RY && kd != SV_RZ && kd != SV_CZ && kd != SV_MAT1) ok = false;
+            // a double excitation needs four register bits
+            if (kd != SV_RY && kd != SV_RZ && kd != SV_CZ && kd != SV_MAT1 && !(pairs && kd == SV_GIVENS) &&
+                !(pairs && kd == SV_DEXC && r == 4))
+                ok = false;
         }
         if (!ok) continue;
         const uint32_t all = (gp.k >= 32) ? 0xFFFFFFFFu : ((1u << gp.k) - 1u);
         auto tmask = [&](const DevOp &d) {
             uint32_t m = 0;
-            const int nq = (d.kind == SV_CZ) ? 2 : 1;
+            const int nq = op_qubits(d.kind);
             for (int i = 0; i < nq; ++i)
                 if (d.t[i] < kOutTarget) m |= 1u << d.t[i];
             return m;
@@ -569,7 +575,7 @@ bool diag_run_pays(const std::vector<DevOp> &run) {
 void plan_steps(QsuPlan &P, int max_diag, int amp) {
     auto tm = [](const DevOp &d) {
         uint32_t m = 0;
-        const int nq = d.kind == SV_CZ ? 2 : 1;
+        const int nq = op_qubits(d.kind);
         for (int i = 0; i < nq; ++i)
             if (d.t[i] >= 0 && d.t[i] < kOutTarget) m |= 1u << d.t[i];
         return m;
@@ -1142,7 +1148,7 @@ std::string plan_qsu(int n, int g, const sv_gate *gates, size_t m, bool lazy, co
     if (P.tiles.empty()) P.final_l2p = l2p_init;
     int k = std::max(o.tile_bits, std::min(o.low_bits, P.nL) + 4);
     plan_gate_passes(P, ops, k, o.low_bits, o.fuse_max, o.diag_exempt);
-    plan_phases(P);
+    plan_phases(P, o.reg_pairs);
     plan_steps(P, std::min(o.max_diag, kMaxPassDiag), o.amp_bytes);
     return "";
 }

@@ -201,6 +201,7 @@ struct PlanOptions {
     int hier_intra = -1;         // >= 0: hierarchical tiling (Alg. 4/5) with this many intra qubits
     int max_diag = kMaxPassDiag; // diagonal blocks per register-blocked pass (shared-memory budget)
     int amp_bytes = 8;           // 8 complex64, 16 complex128 (shared-memory budget of the blocks)
+    bool reg_pairs = true;       // Givens / double excitations may run in register phases
     bool diag_exempt = false;    // QSU: diagonal gates (RZ, CZ) never ask for a QR (per-chunk phases)
     // One greedy step of Alg. 6 done elsewhere (on the device): given the
     // distinct X/Y supports xs with remaining weights w, return the rank of
