@@ -1965,6 +1965,82 @@ __device__ __forceinline__ R evc_fast(const Cx<R> *t, const Cx<R> *own, uint32_t
 // at element frequency w, lane frequency tau mod 32 and warp frequency
 // tau >> 5.  Cost per coset: one transform per group and needed part (Re,
 // Im), independent of the group's string count.
+// Walsh fold of N = 2^L values without touching them: sum_j (-1)^{parity(j & w)} val[j].
+template <typename R, int N>
+__device__ __forceinline__ R walsh_sum_ro(const R *val, uint32_t w) {
+    R tmp[N / 2];
+    const R s0 = sign_of_bit<R>(w, 0);
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) tmp[k] = fma(s0, val[2 * k + 1], val[2 * k]);
+#pragma unroll
+    for (int i = 1, n = N / 2; n > 1; ++i, n >>= 1) {
+        const R sg = sign_of_bit<R>(w, i);
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) tmp[k] = fma(sg, tmp[2 * k + 1], tmp[2 * k]);
+    }
+    return tmp[0];
+}
+
+// Per-string constants of a general EVC pass (complex64 transform-capable
+// passes), staged once per CTA: the signs of the element Walsh fold per level
+// (frequency w = bz >> log2(512 / 2^kl), with the pair-split bit removed when
+// the group splits), z, the thread-sign mask tz (parity(tid & tz) =
+// parity(l & z) ^ parity(a0 & bz)) and flags: bit 0 the part (nY odd: Im),
+// bit 1 the i^nY sign, bit 2 the split bit of w.
+struct StrC {
+    float4 lev;
+    uint64_t z;
+    uint32_t tz, flags;
+};
+static_assert(sizeof(StrC) == 32, "StrC layout");
+
+template <int N>
+__device__ __forceinline__ float walsh_lev(const float *val, const float4 &lev) {
+    const float sg[4] = {lev.x, lev.y, lev.z, lev.w};
+    float tmp[N / 2];
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) tmp[k] = fmaf(sg[0], val[2 * k + 1], val[2 * k]);
+#pragma unroll
+    for (int i = 1, n = N / 2; n > 1; ++i, n >>= 1) {
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) tmp[k] = fmaf(sg[i], tmp[2 * k + 1], tmp[2 * k]);
+    }
+    return tmp[0];
+}
+
+// Re and Im of conj(partner) * own for the thread's 16 elements (complex64,
+// 512 threads): partner of element j is t[(tid + 512 j) ^ X]; X = 0 gives
+// |own|^2 and 0.
+__device__ __forceinline__ void pair_terms_all(const float2 *t, const float2 *own, uint32_t X, float *vr, float *vi) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float2 u = own[j];
+        if (X) {
+            const float2 w = t[(threadIdx.x + j * 512u) ^ X];
+            vr[j] = w.x * u.x + w.y * u.y;
+            vi[j] = w.x * u.y - w.y * u.x;
+        } else {
+            vr[j] = u.x * u.x + u.y * u.y;
+            vi[j] = 0.f;
+        }
+    }
+}
+// The same for the 8 elements j with bit H of j equal to S (one element of
+// every pair), as j' = j with bit H removed.
+template <int H, int S>
+__device__ __forceinline__ void pair_terms_sel(const float2 *t, const float2 *own, uint32_t X, float *vr, float *vi) {
+    const uint32_t sb = smem_u32(t);
+    const uint32_t B = ((threadIdx.x ^ X) * 8u) ^ ((uint32_t)S << (H + 12));
+#pragma unroll
+    for (int jp = 0; jp < 8; ++jp) {
+        const int j0 = ((jp >> H) << (H + 1)) | (jp & ((1 << H) - 1));
+        const float2 u = own[j0 | (S << H)];
+        const float2 w = lds_cx<float>(sb + (B ^ ((uint32_t)j0 << 12)));
+        vr[jp] = w.x * u.x + w.y * u.y;
+        vi[jp] = w.x * u.y - w.y * u.x;
+    }
+}
+
 constexpr int kXformMinStrings = 16;  // groups with at least this many strings take the transform path
 constexpr int kXformScratch = 8192;   // floats of shared scratch (16 element x 16 warp x 32 lane frequencies)
 
@@ -2010,6 +2086,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
     uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
     double *acc = reinterpret_cast<double *>(spanv + (1u << a.m));
     float *scr = reinterpret_cast<float *>(acc + nslots * nwarps);     // transform scratch (when xform)
+    StrC *strc = reinterpret_cast<StrC *>(scr + kXformScratch);         // per-string constants (when xform)
     for (int j = threadIdx.x; j < nslots * nwarps; j += blockDim.x) acc[j] = 0.0;
     coset_span(a, spanv);
     const ThreadCoset tc = thread_coset(a.kl);
@@ -2019,6 +2096,30 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
     if constexpr (sizeof(R) == 4 && EPT == 16) {
         use_x = xform && blockDim.x == 512 && E == 8192u;
         for (int b = 0; b < 5; ++b) lsg[b] = ((lane >> b) & 1) ? -1.f : 1.f;
+        if (use_x) {
+            // the pair-split bit of a group is the same in every thread (only its side differs)
+            for (int gi = a.g_begin + warp; gi < a.g_end; gi += nwarps) {
+                const DevGroup G = groups[gi];
+                const int h = G.X ? pair_split(tc, G.X, a.kl, 16).h : -1;
+                for (int q = G.s_begin + lane; q < G.s_end; q += 32) {
+                    const DevString S = strs[q];
+                    const uint32_t w = S.bz >> tc.ash;
+                    uint32_t wf = w, flip = 0;
+                    if (h >= 0) {
+                        wf = (w & ((1u << h) - 1u)) | ((w >> (h + 1)) << h);
+                        flip = (w >> h) & 1u;
+                    }
+                    StrC c;
+                    c.lev = make_float4((wf & 1u) ? -1.f : 1.f, (wf & 2u) ? -1.f : 1.f, (wf & 4u) ? -1.f : 1.f,
+                                        (wf & 8u) ? -1.f : 1.f);
+                    c.z = S.z;
+                    c.tz = (uint32_t)(S.z & ((1ull << a.kl) - 1ull)) | ((S.bz & ((1u << tc.ash) - 1u)) << a.kl);
+                    const uint32_t neg0 = G.X ? (uint32_t)((S.nY == 1) | (S.nY == 2)) : 0u;
+                    c.flags = (uint32_t)(S.nY & 1) | (neg0 << 1) | (flip << 2);
+                    strc[q - a.s_begin] = c;
+                }
+            }
+        }
     }
     const uint64_t ncos = 1ull << a.nfree;
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -2047,32 +2148,45 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
             const DevGroup G = groups[gi];
             if constexpr (sizeof(R) == 4 && EPT == 16) {
                 const int K = G.s_end - G.s_begin;
-                if (use_x && K >= 2 && K < kXformMinStrings) {
-                    // a few strings: the pair terms of every element once, then per string a
-                    // Walsh fold over the element bits, the thread and coset signs, a warp sum
+                if (use_x && K < kXformMinStrings) {
+                    // up to 15 strings: the Re and Im pair terms of the thread's elements once
+                    // (one element of every pair when the split allows, else all of them),
+                    // then per string a Walsh fold and the thread / coset sign; four
+                    // strings share one warp reduction
+                    const PairSel ps = G.X ? pair_split(tc, G.X, a.kl, 16) : PairSel{-1, 0, 1};
                     float vr[16], vi[16];
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const Cx<R> u = own[j];
-                        if (G.X) {
-                            const Cx<R> w = t[(threadIdx.x + j * 512u) ^ G.X];
-                            vr[j] = w.x * u.x + w.y * u.y;
-                            vi[j] = w.x * u.y - w.y * u.x;
-                        } else {
-                            vr[j] = u.x * u.x + u.y * u.y;
-                            vi[j] = 0.f;
-                        }
+#define SV_PT(HH) \
+    case HH: if (ps.s) pair_terms_sel<HH, 1>(t, own, G.X, vr, vi); else pair_terms_sel<HH, 0>(t, own, G.X, vr, vi); break;
+                    switch (ps.h) {
+                        SV_PT(0) SV_PT(1) SV_PT(2) SV_PT(3)
+                    default: pair_terms_all(t, own, G.X, vr, vi); break;
                     }
-                    for (int q = G.s_begin; q < G.s_end; ++q) {
-                        const DevString S = strs[q];
-                        float f[16];
+#undef SV_PT
+                    const float fac = (float)ps.fac;
+                    const bool split = ps.h >= 0;
+                    for (int q0 = G.s_begin; q0 < G.s_end; q0 += 4) {
+                        float c[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) f[j] = (S.nY & 1) ? vi[j] : vr[j];
-                        float c = walsh_sum<float, 16>(f, S.bz >> tc.ash);
-                        const int neg = (__popcll((rep | tc.l) & S.z) ^ __popc(tc.a0 & S.bz) ^
-                                         (G.X ? ((S.nY == 1) | (S.nY == 2)) : 0)) & 1;
-                        c = warp_sum<float>(neg ? -c : c);
-                        if (lane == 0) acc[(q - a.s_begin) * nwarps + warp] += (double)c;
+                        for (int k = 0; k < 4; ++k) {
+                            if (q0 + k < G.s_end) {
+                                const StrC C = strc[q0 + k - a.s_begin];
+                                float r;
+                                if (split) {
+                                    // the fold over j' (bit h of j removed); the side s flips by w's bit h
+                                    r = (C.flags & 1u) ? walsh_lev<8>(vi, C.lev) : walsh_lev<8>(vr, C.lev);
+                                    if (ps.s & (C.flags >> 2)) r = -r;
+                                } else {
+                                    r = (C.flags & 1u) ? walsh_lev<16>(vi, C.lev) : walsh_lev<16>(vr, C.lev);
+                                }
+                                const uint32_t neg = ((uint32_t)__popcll(rep & C.z) ^ (uint32_t)__popc(threadIdx.x & C.tz) ^
+                                                      (C.flags >> 1)) & 1u;
+                                c[k] = neg ? -r * fac : r * fac;
+                            }
+                        }
+                        const float red = warp_sum4<float>(c[0], c[1], c[2], c[3]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (lane == 8 * k && q0 + k < G.s_end) acc[(q0 + k - a.s_begin) * nwarps + warp] += (double)red;
                     }
                     continue;
                 }
@@ -3301,8 +3415,9 @@ cudaError_t evc_dispatch(cudaStream_t st, int grid, const void *psi, const Coset
     size_t sm = coset_smem(sizeof(R) == 4 ? SV_C64 : SV_C128, E, a.m, a.s_end - a.s_begin, threads / 32);
     // transform scratch for large groups (complex64, 16 per thread, 512 threads) when it fits
     int xform = 0;
-    if (sizeof(R) == 4 && threads == 512 && E == 8192 && sm + kXformScratch * 4 <= (size_t)smem_optin()) {
-        sm += kXformScratch * 4;
+    const size_t strc_bytes = (size_t)(a.s_end - a.s_begin) * sizeof(StrC);
+    if (sizeof(R) == 4 && threads == 512 && E == 8192 && sm + kXformScratch * 4 + strc_bytes <= (size_t)smem_optin()) {
+        sm += kXformScratch * 4 + strc_bytes;
         xform = 1;
     }
 #define SV_EVC_CASE(N)                                                                                       \

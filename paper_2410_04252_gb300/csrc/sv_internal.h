@@ -13,7 +13,7 @@ namespace sv {
 constexpr int kMaxQubits = 40;
 constexpr int kMaxSpan = 10;         // coset dimension limit of an EVC / H|psi> pass
 constexpr int kMaxRunBits = 7;       // longest contiguous run of a coset pass (2^7 amplitudes)
-constexpr int kMaxPassStrings = 512; // strings per EVC pass (shared-memory accumulators)
+constexpr int kMaxPassStrings = 384; // strings per EVC pass (shared-memory accumulators and constants)
 constexpr int kMaxPassOps = 256;       // gates per shared-memory pass
 constexpr int kMaxGroupStrings = 256; // distinct Z masks sharing one X/Y mask in one group
 
