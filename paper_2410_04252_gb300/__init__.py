@@ -5,11 +5,12 @@ Submodules:
   workloads  seeded synthetic circuits, parameters and Hamiltonians
   sv         ctypes binding of the C-ABI library libsv.so (CUDA, sm_103a)
   autograd   torch.autograd.Function over sv_grad
+  dist       the state sharded over ranks: QRs as pairwise exchanges
 
 The binding is imported on first use of a name it defines, so that the
 input generators can be used without loading CUDA.
 """
-__all__ = ["workloads", "sv", "autograd"]
+__all__ = ["workloads", "sv", "autograd", "dist"]
 
 
 def __getattr__(name):
