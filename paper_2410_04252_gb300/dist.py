@@ -232,3 +232,32 @@ def sharded_energy(n: int, circ, params, ham, chunk, init_index: int = 0, group=
         l2p = t["l2p"]
     vals = allreduce_sum(vals, group, chunk.device if dist.get_backend(group) == "nccl" else None)
     return float(np.dot(ham.coeffs, vals)), vals, l2p
+
+
+# ----------------------------------------------------------- cost model --
+
+def qr_kinds(plan: dict, n: int) -> list[str]:
+    """Per QR of a plan (sv.plan_qsu / plan_evc dict), 'intra' or 'inter'
+    (Fig. 7): a QR is an inter QR when the inter set Q \\ (Q_L u Q_intra)
+    changes, i.e. amplitudes cross nodes; otherwise they stay in a node."""
+    full = (1 << n) - 1
+    kinds, prev = [], None
+    for t in plan["tiles"]:
+        inter = full & ~(t["local_mask"] | t.get("intra_mask", 0))
+        if t["pairs"]:
+            kinds.append("inter" if prev is None or inter != prev else "intra")
+        prev = inter
+    return kinds
+
+
+def qr_weight(n: int, g: int, s: int, amp_bytes: int, bandwidth_gbs: float) -> float:
+    """Seconds of one QR of s pairs on 2^g ranks: every rank sends (and
+    receives) 1 - 2^-s of its chunk of 2^(n - g) amplitudes over a link of
+    the given bandwidth."""
+    return (1.0 - 2.0 ** -s) * (1 << (n - g)) * amp_bytes / (bandwidth_gbs * 1e9)
+
+
+def comm_cost(plan: dict, n: int, w_intra: float, w_inter: float) -> float:
+    """Eq. comm_cost: w_intra * N_intra + w_inter * N_inter over the plan's QRs."""
+    k = qr_kinds(plan, n)
+    return w_intra * k.count("intra") + w_inter * k.count("inter")

@@ -173,3 +173,23 @@ def test_sharded_energy_matches_single_buffer(world):
     ref = oracle.expect_terms(oracle.apply_circuit(oracle.basis_state(n, 0), circ, params), ham).real
     assert np.max(np.abs(vals - ref)) < 1e-12
     assert abs(e - float(ham.coeffs @ ref)) < 1e-12
+
+
+def test_comm_cost_of_fig9():
+    """Eq. comm_cost on the hierarchical plan of Fig. 9 (2 inter and 3 intra
+    QRs), with weights from link bandwidths (one QR of s pairs moves 1 - 2^-s
+    of a rank's chunk)."""
+    from paper_2410_04252_gb300 import dist as D
+    from paper_2410_04252_gb300 import sv
+    from paper_2410_04252_gb300 import workloads as W
+    n, nL = 16, 12
+    c = W.fabric_blocks_circuit(n, 12)
+    o = sv.default_options()
+    o.intra_bits = 2
+    plan = sv.plan_qsu(n, n - nL, c, sv.HIER, o)
+    assert D.qr_kinds(plan, n) == ["inter", "intra", "intra", "inter", "intra"]
+    assert D.comm_cost(plan, n, 1.0, 20.0) == 2 * 20.0 + 3 * 1.0
+    w = D.qr_weight(30, 5, 2, 16, 100.0)
+    assert w == pytest.approx(0.75 * (1 << 25) * 16 / 100e9)
+    flat = sv.plan_qsu(n, n - nL, c, sv.LAZY)
+    assert D.qr_kinds(flat, n) == ["inter"] * 3     # no intra set: every QR crosses nodes
