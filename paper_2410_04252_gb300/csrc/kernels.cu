@@ -2425,6 +2425,191 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_few(const Cx<R> *__restri
     }
 }
 
+// ---- K-EVC few-string pass, three-stage ring --------------------------
+// The pass of k_evc_few's fast layout (512 threads, EPT elements each, E =
+// 512 EPT) with every per-group constant set once per launch: per thread the
+// partner base address of the pair split (side included), the fold code and
+// the constant part of the sign; per group (shared) the signs of the element
+// Walsh fold per level.  Cosets stream through three shared buffers, so the
+// copies of coset it + 2 are issued right after the one barrier of iteration
+// it and two cosets are in flight while one is evaluated.
+
+template <typename R> struct LevT { R s[4]; };
+
+// sum over the selected elements (bit H of j equal to S; j' = j with bit H
+// removed) of the pair term, folded by the level signs
+template <typename R, int EPT, int H, int S, bool ODD>
+__device__ __forceinline__ R evc_sel2(uint32_t sb, const Cx<R> *own, uint32_t B, const LevT<R> &lv) {
+    constexpr int SH = 9 + (sizeof(R) == 4 ? 3 : 4);
+    constexpr int N = EPT / 2;
+    R val[N];
+#pragma unroll
+    for (int jp = 0; jp < N; ++jp) {
+        const int j0 = ((jp >> H) << (H + 1)) | (jp & ((1 << H) - 1));
+        const Cx<R> u = own[j0 | (S << H)];
+        const Cx<R> v = lds_cx<R>(sb + (B ^ ((uint32_t)j0 << SH)));
+        val[jp] = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
+    }
+#pragma unroll
+    for (int i = 0, n = N; n > 1; ++i, n >>= 1) {
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) val[k] = fma(lv.s[i], val[2 * k + 1], val[2 * k]);
+    }
+    return val[0];
+}
+// every element (no split; X = 0 gives |own|^2)
+template <typename R, int EPT, bool ODD>
+__device__ __forceinline__ R evc_all2(uint32_t sb, const Cx<R> *own, uint32_t B, bool diag, const LevT<R> &lv) {
+    constexpr int SH = 9 + (sizeof(R) == 4 ? 3 : 4);
+    R val[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const Cx<R> u = own[j];
+        if (diag) {
+            val[j] = u.x * u.x + u.y * u.y;
+        } else {
+            const Cx<R> v = lds_cx<R>(sb + (B ^ ((uint32_t)j << SH)));
+            val[j] = ODD ? (v.x * u.y - v.y * u.x) : (v.x * u.x + v.y * u.y);
+        }
+    }
+#pragma unroll
+    for (int i = 0, n = EPT; n > 1; ++i, n >>= 1) {
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) val[k] = fma(lv.s[i], val[2 * k + 1], val[2 * k]);
+    }
+    return val[0];
+}
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ psi, const CosetArgs a,
+                                                     const DevGroup *__restrict__ groups,
+                                                     const DevString *__restrict__ strs, double *__restrict__ part,
+                                                     int part_stride) {
+    constexpr int NT = 512;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t E = 1u << (a.kl + a.m);
+    const int ng = a.g_end - a.g_begin;          // == number of strings (one per group), at most kEvcFew
+    Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
+    uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 3 * (size_t)E);
+    __shared__ LevT<R> glev[kEvcFew];
+    __shared__ uint64_t gz[kEvcFew];
+    __shared__ R gfac[kEvcFew];
+    __shared__ double wsum[kEvcFew][NT / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < kEvcFew * (NT / 32); j += NT) wsum[j / (NT / 32)][j % (NT / 32)] = 0.0;
+    coset_span(a, spanv);
+    const ThreadCoset tc = thread_coset(a.kl);
+    // per group: packed per-thread constants (partner base | code << 20 | sign bit 31)
+    uint32_t pk[kEvcFew];
+    uint32_t tmask = 0;
+#pragma unroll
+    for (int g = 0; g < kEvcFew; ++g) {
+        pk[g] = 0;
+        if (g < ng) {
+            const DevGroup G = groups[a.g_begin + g];
+            const DevString S = strs[G.s_begin];
+            const uint32_t w = S.bz >> tc.ash;
+            const PairSel ps = G.X ? pair_split(tc, G.X, a.kl, EPT) : PairSel{-1, 0, 1};
+            uint32_t wf = w, flip = 0;
+            if (ps.h >= 0) {
+                wf = (w & ((1u << ps.h) - 1u)) | ((w >> (ps.h + 1)) << ps.h);
+                flip = (uint32_t)ps.s & (w >> ps.h) & 1u;
+            }
+            const uint32_t neg0 = G.X ? (uint32_t)((S.nY == 1) | (S.nY == 2)) : 0u;
+            const uint32_t tconst = ((uint32_t)__popc(tc.l & (uint32_t)S.z) ^ (uint32_t)__popc(tc.a0 & S.bz) ^ neg0 ^
+                                     flip) & 1u;
+            constexpr int SH = 9 + (sizeof(R) == 4 ? 3 : 4);
+            uint32_t B = (threadIdx.x ^ G.X) * (uint32_t)sizeof(Cx<R>);
+            if (ps.h >= 0) B ^= (uint32_t)ps.s << (ps.h + SH);
+            const uint32_t code = G.X ? ((uint32_t)(ps.h + 1) | ((uint32_t)ps.s << 3) | ((uint32_t)(S.nY & 1) << 4))
+                                      : 31u;   // 31: the diagonal group
+            pk[g] = B | (code << 20);
+            tmask |= tconst << g;
+            if (threadIdx.x == 0) {
+                LevT<R> lv;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) lv.s[i] = ((wf >> i) & 1u) ? (R)-1 : (R)1;
+                glev[g] = lv;
+                gz[g] = S.z;
+                gfac[g] = (R)ps.fac;
+            }
+        }
+    }
+    __syncthreads();
+    const uint64_t ncos = 1ull << a.nfree;
+    const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
+    uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
+    for (uint64_t k = 0; k < 2; ++k) {
+        if (k < mine) load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
+        cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
+    }
+    R acc[kEvcFew];
+#pragma unroll
+    for (int g = 0; g < kEvcFew; ++g) acc[g] = 0;
+    for (uint64_t it = 0; it < mine; ++it) {
+        const uint64_t rep = rep_cur;
+        rep_cur = walk_next(rep_cur, bw);
+        cp_async_wait1();
+        __syncthreads();
+        // coset it + 2 into the buffer of coset it - 1 (every thread is past it)
+        if (it + 2 < mine) load_coset<R>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, a.kl, E);
+        cp_async_commit();
+        rep_pf = walk_next(rep_pf, bw);
+        const Cx<R> *t = buf + (it % 3) * E;
+        const uint32_t sb = smem_u32(t);
+        Cx<R> own[EPT];
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) own[j] = t[threadIdx.x + j * NT];
+        const uint32_t bmask =
+            tmask ^ __ballot_sync(0xffffffffu, lane < ng && ((__popcll(rep & gz[lane < ng ? lane : 0]) & 1) != 0));
+#pragma unroll
+        for (int g = 0; g < kEvcFew; ++g) {
+            if (g < ng) {
+                const uint32_t B = pk[g] & 0xFFFFFu, code = pk[g] >> 20;
+                const LevT<R> lv = glev[g];
+                R v;
+                switch (code) {
+                case 0: v = evc_all2<R, EPT, false>(sb, own, B, false, lv); break;
+                case 16: v = evc_all2<R, EPT, true>(sb, own, B, false, lv); break;
+                case 31: v = evc_all2<R, EPT, false>(sb, own, B, true, lv); break;
+#define SV_SEL2(HH, SS, OO)                                                                                  \
+    case (HH + 1) | (SS << 3) | (OO << 4):                                                                   \
+        if constexpr ((2 << HH) <= EPT) v = evc_sel2<R, EPT, HH, SS, OO != 0>(sb, own, B, lv);               \
+        else v = 0;                                                                                          \
+        break;
+#define SV_SEL2_4(HH) SV_SEL2(HH, 0, 0) SV_SEL2(HH, 1, 0) SV_SEL2(HH, 0, 1) SV_SEL2(HH, 1, 1)
+                    SV_SEL2_4(0) SV_SEL2_4(1) SV_SEL2_4(2) SV_SEL2_4(3)
+#undef SV_SEL2_4
+#undef SV_SEL2
+                default: v = 0; break;
+                }
+                acc[g] += ((bmask >> g) & 1u) ? -v : v;
+            }
+        }
+        if ((it & 63) == 63 || it + 1 == mine) {
+            // flush: FP64 warp sums (times the pair factor) into the per-warp slots (fixed order)
+#pragma unroll
+            for (int g = 0; g < kEvcFew; ++g) {
+                if (g < ng) {
+                    double v = (double)acc[g] * (double)gfac[g];
+                    acc[g] = 0;
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) wsum[g][warp] += v;
+                }
+            }
+        }
+    }
+    cp_async_wait0();
+    __syncthreads();
+    if (threadIdx.x < ng) {
+        double tsum = 0.0;
+        for (int w = 0; w < NT / 32; ++w) tsum += wsum[threadIdx.x][w];
+        part[(size_t)blockIdx.x * part_stride + a.s_begin + threadIdx.x] = tsum;
+    }
+}
+
 // ------------------------------------------------------------------ K-HPSI --
 // lambda[b] += sum_t a_t i^nY (-1)^{|(b^x)&z|} psi[b^x] for every group of the
 // pass (P|c> = i^nY (-1)^{|c&z|} |c^x>, c = b^x; parity((b^x)&z) =
@@ -3392,6 +3577,24 @@ cudaError_t evc_dispatch(cudaStream_t st, int grid, const void *psi, const Coset
     // threads: a multiple of the run length, at least one warp, at most 512
     const int threads = std::max(std::max(32, 1 << a.kl), std::min(E, 512));
     const int ept = std::max(1, E / threads);
+    if (a.few && threads == 512 && ept >= 2 && ept <= 16 && E == (uint32_t)ept * 512u &&
+        3 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8 + 4096 <= (size_t)smem_optin()) {
+        const size_t smr = 3 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8;
+#define SV_EVCR_CASE(N)                                                                                      \
+    case N:                                                                                                  \
+        allow_smem(k_evc_ring<R, N>, smr);                                                                   \
+        k_evc_ring<R, N><<<grid, 512, smr, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride);    \
+        return cudaGetLastError();
+        switch (ept) {
+            SV_EVCR_CASE(2)
+            SV_EVCR_CASE(4)
+            SV_EVCR_CASE(8)
+            SV_EVCR_CASE(16)
+        default:
+            break;
+        }
+#undef SV_EVCR_CASE
+    }
     if (a.few) {
         const size_t smf = 2 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8 +
                            (size_t)kEvcFew * threads * (sizeof(R) + 4);
