@@ -2969,6 +2969,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
     R *coef = reinterpret_cast<R *>(opacc + (size_t)kBatchMaxOps * nwarps);   // [2 * kBatchMaxGates]
     __shared__ int s_state;
     __shared__ double s_red[32];
+    __shared__ HpsiTab tabs;
     const size_t N = (size_t)1 << a.n;
     Cx<R> *psi = reinterpret_cast<Cx<R> *>(a.work) + (size_t)blockIdx.x * 2 * N;
     Cx<R> *lam = psi + N;
@@ -3047,10 +3048,34 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                     if (j >> i & 1u) v ^= C.basis[i];
                 spanv[j] = v;
             }
-            __syncthreads();
             const ThreadCoset tc = thread_coset(C.kl);
             const uint64_t ncos = 1ull << C.nfree;
             const bool fast = (NT == 512) && (E == (uint32_t)EPT * 512u);
+            // the pass's strings staged once (as in k_hpsi_pass); the table of
+            // the previous pass is no longer read (barrier at its end)
+            int ns = 0;
+            uint32_t tmask = 0;
+            if constexpr (sizeof(R) == 4 && EPT == 16) {
+                if (fast) {
+                    for (int gi = C.g_begin; gi < C.g_end; ++gi) {
+                        const DevGroup G = a.groups[gi];
+                        for (int sidx = G.s_begin; sidx < G.s_end; ++sidx, ++ns) {
+                            if (ns >= kHpsiTab) continue;
+                            const DevString S = a.strs[sidx];
+                            tmask |= (uint32_t)((__popcll(tc.l & S.z) ^ __popc(tc.a0 & S.bz) ^ S.nY) & 1) << ns;
+                            if (threadIdx.x == 0) {
+                                const float gf = (S.nY & 2) ? -(float)S.coef : (float)S.coef;
+                                tabs.z[ns] = S.z;
+                                tabs.X[ns] = G.X | ((uint32_t)(S.nY & 1) << 31);
+                                tabs.g[ns] = __float_as_uint(gf);
+                                tabs.w[ns] = S.bz >> tc.ash;
+                            }
+                        }
+                    }
+                }
+            }
+            const bool tabbed = ns > 0 && ns <= kHpsiTab;
+            __syncthreads();
             // cosets alternate between the two buffers (lambda's buffer is free
             // here); the next one streams in while the current one is used
             load_coset<R>(tp, psi, deposit(0, C.freeb, C.nfree), spanv, C.kl, E);
@@ -3069,7 +3094,16 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                 }
                 cp_async_wait1();
                 __syncthreads();
-                for (int gi = C.g_begin; gi < C.g_end; ++gi) {
+                if constexpr (sizeof(R) == 4 && EPT == 16) {
+                    if (tabbed) {
+                        const bool pb = lane < ns && ((__popcll(rep & tabs.z[lane < ns ? lane : 0]) & 1) != 0);
+                        const uint32_t bmask = tmask ^ __ballot_sync(0xffffffffu, pb);
+                        const uint32_t sb = smem_u32(cur);
+                        for (int k = 0; k < ns; ++k)
+                            hpsi_tab_string(reinterpret_cast<float2 *>(acc), tabs, k, sb, bmask);
+                    }
+                }
+                for (int gi = tabbed ? C.g_end : C.g_begin; gi < C.g_end; ++gi) {
                     const DevGroup G = a.groups[gi];
                     for (int s = G.s_begin; s < G.s_end; ++s) {
                         const DevString S = a.strs[s];
