@@ -1233,8 +1233,11 @@ __device__ __forceinline__ void load_tile_async(E *tile, const Cx<R> *psi, uint6
 // Shared-memory layout of a register-blocked pass (both kernels): the tiles,
 // then these tables (offsets in bytes from the end of the tiles).
 struct RegLayout {
-    uint32_t hioff, cs, steps, blocks, mem, pbase, prb, acc, area, total;
+    uint32_t hioff, cs, steps, blocks, mem, pbase, prb, acc, tot, area, total;
 };
+// FP64 is 1/64 of the FP32 rate on this part: per-tile gradient partials stay
+// in FP32 slots and reach FP64 once every kAdjFlush tiles
+constexpr uint64_t kAdjFlush = 16;
 __host__ __device__ inline uint32_t align16u(uint32_t v) { return (v + 15u) & ~15u; }
 __host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, bool adj) {
     RegLayout L;
@@ -1248,7 +1251,10 @@ __host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, 
     L.mem = o;   o = align16u(o + (uint32_t)sizeof(DiagMember) * (uint32_t)(a.mem_end - a.mem_begin));
     L.pbase = o; o = align16u(o + 2u * kRegThreads * nph);
     L.prb = o;   o = align16u(o + 8u * nph);
-    L.acc = o;   o = align16u(o + (adj ? 8u * (kRegThreads / 32) * nops : 0u));
+    // adjoint gradient slots: per op and warp a partial of the state's real
+    // type, and for complex64 an FP64 total per op (flushed every kAdjFlush tiles)
+    L.acc = o;   o = align16u(o + (adj ? ((uint32_t)amp / 2u) * (kRegThreads / 32) * nops : 0u));
+    L.tot = o;   o = align16u(o + (adj && amp == 8 ? 8u * nops : 0u));
     L.area = o;  o = align16u(o + (uint32_t)a.area);
     L.total = o;
     return L;
@@ -1468,8 +1474,11 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     RA<R> *tp = tl + T;
     unsigned char *sm = smem + 2 * T * sizeof(RA<R>);
     const RegLayout L = reg_layout(a, (int)sizeof(Cx<R>), true);
-    double *acc = reinterpret_cast<double *>(sm + L.acc);
-    for (int j = threadIdx.x; j < nops * nwarps; j += NT) acc[j] = 0.0;
+    R *acc = reinterpret_cast<R *>(sm + L.acc);
+    double *tot64 = reinterpret_cast<double *>(sm + L.tot);
+    for (int j = threadIdx.x; j < nops * nwarps; j += NT) acc[j] = 0;
+    if constexpr (sizeof(R) == 4)
+        for (int j = threadIdx.x; j < nops; j += NT) tot64[j] = 0.0;
     reg_setup<R, RB>(sm, L, a, ops, phases, steps, coef, dblocks, dmem, true);
     __syncthreads();
     const uint64_t *hioff = reinterpret_cast<const uint64_t *>(sm + L.hioff);
@@ -1539,7 +1548,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
 #pragma unroll
                     for (int b = 0; b < RB; ++b) {
                         if (!((S.a >> b) & 1)) continue;
-                        if (lane == 8 * b) acc[o * nwarps + warp] += (double)tot;
+                        if (lane == 8 * b) acc[o * nwarps + warp] += tot;
                         ++o;
                         const Cx<R> k = *c++;
                         const RotK<R> rk = rotk<R>(k.x, k.y);
@@ -1568,7 +1577,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                         for (int mi = B.m_begin; mi < B.m_end; ++mi) {
                             const DiagMember m = mem[mi - a.mem_begin];
                             if (m.type == SV_DM_REG_RZ && lane == 8 * m.a)
-                                acc[(m.op - a.op_begin) * nwarps + warp] += (double)red;
+                                acc[(m.op - a.op_begin) * nwarps + warp] += red;
                         }
                     } else {
                         // thread RZ members: +-tot by the thread's bit, four at a time
@@ -1588,7 +1597,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                             const R red = warp_sum4<R>(vals[0], vals[1], vals[2], vals[3]);
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * nwarps + warp] += (double)red;
+                                if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * nwarps + warp] += red;
                         }
                     }
                     reg_diag<R, RB>(xp, B, area);
@@ -1599,7 +1608,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     R g = ra_adjoint_op<R, RB>(xp, xl, op, P.rmask, base, cs[S.a - a.op_begin], mats);
                     if (has_param(op.kind)) {
                         g = warp_sum<R>(g);
-                        if (lane == 0) acc[(S.a - a.op_begin) * nwarps + warp] += (double)g;
+                        if (lane == 0) acc[(S.a - a.op_begin) * nwarps + warp] += g;
                     }
                 }
             }
@@ -1621,10 +1630,26 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
             }
         }
         __syncthreads();
+        if constexpr (sizeof(R) == 4) {
+            // the next writes to the slots follow the next tile's barrier
+            if (((it + 1) % kAdjFlush) == 0 || it + 1 == mine) {
+                for (int o = threadIdx.x; o < nops; o += NT) {
+                    float f = 0.f;
+                    for (int w = 0; w < nwarps; ++w) {
+                        f += acc[o * nwarps + w];
+                        acc[o * nwarps + w] = 0.f;
+                    }
+                    tot64[o] += (double)f;
+                }
+            }
+        }
     }
+    __syncthreads();
     for (int o = threadIdx.x; o < nops; o += NT) {
         double tsum = 0.0;
-        for (int w = 0; w < nwarps; ++w) tsum += acc[o * nwarps + w];
+        if constexpr (sizeof(R) == 4) tsum = tot64[o];
+        else
+            for (int w = 0; w < nwarps; ++w) tsum += acc[o * nwarps + w];
         part[(size_t)blockIdx.x * part_stride + a.op_begin + o] = tsum;
     }
 }
@@ -2042,6 +2067,21 @@ __device__ __forceinline__ void pair_terms_sel(const float2 *t, const float2 *ow
 }
 
 constexpr int kXformMinStrings = 16;  // groups with at least this many strings take the transform path
+// shared-memory layout of k_evc_pass: two staged cosets, the span table, per
+// string and warp a partial of the state's real type (FP64 is 1/64 of the
+// FP32 rate here: complex64 partials reach an FP64 total per string every
+// kEvcFlush cosets), then the transform scratch and string constants
+constexpr uint64_t kEvcFlush = 64;
+__host__ __device__ inline size_t evc_al16(size_t v) { return (v + 15) & ~(size_t)15; }
+__host__ __device__ inline size_t evc_span_end(uint32_t E, int m, size_t rbytes) {
+    return evc_al16(2 * (size_t)E * 2 * rbytes + ((size_t)8 << m));
+}
+__host__ __device__ inline size_t evc_part_bytes(int nslots, int nwarps, size_t rbytes) {
+    return evc_al16((size_t)nslots * nwarps * rbytes);
+}
+__host__ __device__ inline size_t evc_slot_bytes(int nslots, int nwarps, size_t rbytes) {
+    return evc_part_bytes(nslots, nwarps, rbytes) + (rbytes == 4 ? evc_al16((size_t)nslots * 8) : 0);
+}
 constexpr int kXformScratch = 8192;   // floats of shared scratch (16 element x 16 warp x 32 lane frequencies)
 
 __device__ __forceinline__ void xform_part(float *v, float *scr, const float *lsg) {
@@ -2084,10 +2124,14 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
     const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
     uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 2 * E);
-    double *acc = reinterpret_cast<double *>(spanv + (1u << a.m));
-    float *scr = reinterpret_cast<float *>(acc + nslots * nwarps);     // transform scratch (when xform)
+    unsigned char *slots = smem + evc_span_end(E, a.m, sizeof(R));
+    R *acc = reinterpret_cast<R *>(slots);                                 // [string][warp] partials
+    double *tot64 = reinterpret_cast<double *>(slots + evc_part_bytes(nslots, nwarps, sizeof(R)));
+    float *scr = reinterpret_cast<float *>(slots + evc_slot_bytes(nslots, nwarps, sizeof(R)));   // transform scratch (when xform)
     StrC *strc = reinterpret_cast<StrC *>(scr + kXformScratch);         // per-string constants (when xform)
-    for (int j = threadIdx.x; j < nslots * nwarps; j += blockDim.x) acc[j] = 0.0;
+    for (int j = threadIdx.x; j < nslots * nwarps; j += blockDim.x) acc[j] = 0;
+    if constexpr (sizeof(R) == 4)
+        for (int j = threadIdx.x; j < nslots; j += blockDim.x) tot64[j] = 0.0;
     coset_span(a, spanv);
     const ThreadCoset tc = thread_coset(a.kl);
     // the transform path needs complex64, 16 per thread, 512 threads, 8192 staged, the scratch
@@ -2186,7 +2230,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
                         const float red = warp_sum4<float>(c[0], c[1], c[2], c[3]);
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
-                            if (lane == 8 * k && q0 + k < G.s_end) acc[(q0 + k - a.s_begin) * nwarps + warp] += (double)red;
+                            if (lane == 8 * k && q0 + k < G.s_end) acc[(q0 + k - a.s_begin) * nwarps + warp] += red;
                     }
                     continue;
                 }
@@ -2216,7 +2260,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
                                                  ((S.bz & ((1u << tc.ash) - 1u)) << a.kl);
                             float c = xform_coef(scr, (S.bz >> tc.ash) & 15u, tau >> 5, tau & 31u);
                             const int neg = (__popcll(rep & S.z) ^ (G.X ? ((S.nY == 1) | (S.nY == 2)) : 0)) & 1;
-                            acc[(q - a.s_begin) * nwarps] += (double)(neg ? -c : c);
+                            acc[(q - a.s_begin) * nwarps] += neg ? -c : c;
                         }
                         __syncthreads();
                     }
@@ -2266,7 +2310,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
                 for (int s = 0; s < kEvcChunk; ++s) {
                     if (s < nc) {
                         const R v = warp_sum<R>(accr[s] * fac);
-                        if (lane == 0) acc[(cs + s - a.s_begin) * nwarps + warp] += (double)v;
+                        if (lane == 0) acc[(cs + s - a.s_begin) * nwarps + warp] += v;
                     }
                 }
             }
@@ -2275,11 +2319,26 @@ __global__ void __launch_bounds__(512, 1) k_evc_pass(const Cx<R> *__restrict__ p
         if (it + 2 < mine) load_coset<R>(t, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
         rep_pf = walk_next(rep_pf, bw);
+        if constexpr (sizeof(R) == 4) {
+            // the next writes to the slots follow the next coset's barrier
+            if (((it + 1) % kEvcFlush) == 0 || it + 1 == mine) {
+                for (int q = threadIdx.x; q < nslots; q += blockDim.x) {
+                    float f = 0.f;
+                    for (int w = 0; w < nwarps; ++w) {
+                        f += acc[q * nwarps + w];
+                        acc[q * nwarps + w] = 0.f;
+                    }
+                    tot64[q] += (double)f;
+                }
+            }
+        }
     }
     __syncthreads();
     for (int s = threadIdx.x; s < nslots; s += blockDim.x) {
         double tsum = 0.0;
-        for (int w = 0; w < nwarps; ++w) tsum += acc[s * nwarps + w];
+        if constexpr (sizeof(R) == 4) tsum = tot64[s];
+        else
+            for (int w = 0; w < nwarps; ++w) tsum += acc[s * nwarps + w];
         part[(size_t)blockIdx.x * part_stride + a.s_begin + s] = tsum;
     }
 }
@@ -2800,6 +2859,7 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
     const bool tabbed = ns > 0 && ns <= kHpsiTab;
     const int lane = threadIdx.x & 31;
     double eacc = 0.0;
+    R eblk = 0;
     for (uint64_t it = 0; it < mine; ++it) {
         const uint64_t rep = rep_cur;
         rep_cur = walk_next(rep_cur, bw);
@@ -2863,14 +2923,21 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
                 eloc += p.x * acc[j].x + p.y * acc[j].y;
             }
         }
-        eacc += (double)eloc;
+        if (last) {
+            // FP32 over up to 64 cosets, then FP64 (1/64 of the FP32 rate here)
+            eblk += eloc;
+            if (((it + 1) & 63) == 0) {
+                eacc += (double)eblk;
+                eblk = 0;
+            }
+        }
         __syncthreads();
         if (it + 2 < mine) load_coset<R>(t, psi, rep_pf, spanv, a.kl, E);
         cp_async_commit();
         rep_pf = walk_next(rep_pf, bw);
     }
     if (last) {
-        double v = eacc;
+        double v = eacc + (double)eblk;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
         __syncthreads();
@@ -2888,7 +2955,7 @@ __global__ void __launch_bounds__(512, 1) k_hpsi_pass(const Cx<R> *__restrict__ 
 // first) and runs, on its own workspace: |psi> = |init>, the QSU gate passes
 // of the state's plan (no virtual chunks), lambda = H psi by the coset passes
 // of the shared Hamiltonian with the energy Re<psi|lambda>, and the adjoint
-// reverse sweep with per-gate FP64 gradient partials.  No CTA ever waits for
+// reverse sweep with per-gate gradient partials (FP64 sums at the end).  No CTA ever waits for
 // another CTA; every barrier is a __syncthreads inside one CTA.  Per-state
 // start/end device times (globaltimer, ns) give the latency distribution.
 
@@ -2922,7 +2989,7 @@ __device__ __noinline__ void batch_reg_forward(Cx<R> *tile, const GatePassArgs &
 
 template <typename R, int RB>
 __device__ __noinline__ void batch_reg_adjoint(Cx<R> *tp, Cx<R> *tl, const GatePassArgs &P, const DevOp *ops,
-                                  const Phase *phases, const R *coef, double *opacc, int o0) {
+                                  const Phase *phases, const R *coef, R *opacc, int o0) {
     constexpr int V = 1 << RB;
     const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int ph = P.ph_end - 1; ph >= P.ph_begin; --ph) {
@@ -2941,7 +3008,7 @@ __device__ __noinline__ void batch_reg_adjoint(Cx<R> *tp, Cx<R> *tl, const GateP
             R g = reg_adjoint<R, RB>(xp, xl, op, F.rmask, base, coef, nullptr);
             if (has_param(op.kind)) {
                 g = warp_sum<R>(g);
-                if (lane == 0) opacc[(o - o0) * nwarps + warp] += (double)g;
+                if (lane == 0) opacc[(o - o0) * nwarps + warp] += g;
             }
         }
 #pragma unroll
@@ -2965,8 +3032,11 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
     Cx<R> *tp = reinterpret_cast<Cx<R> *>(smem);
     Cx<R> *tl = tp + TILE;
     uint64_t *hioff = reinterpret_cast<uint64_t *>(tl + TILE);       // 2^hio entries (>= 2^(k - nlow), >= 256)
-    double *opacc = reinterpret_cast<double *>(hioff + (1u << a.hio));   // [kBatchMaxOps][nwarps]
-    R *coef = reinterpret_cast<R *>(opacc + (size_t)kBatchMaxOps * nwarps);   // [2 * kBatchMaxGates]
+    // per op and warp a gradient partial of the state's real type over the
+    // state's tiles (FP64 is 1/64 of the FP32 rate here), summed in FP64 at the end
+    unsigned char *opbase = reinterpret_cast<unsigned char *>(hioff + (1u << a.hio));
+    R *opacc = reinterpret_cast<R *>(opbase);                                        // [kBatchMaxOps][nwarps]
+    R *coef = reinterpret_cast<R *>(opbase + (size_t)kBatchMaxOps * nwarps * 8);     // [2 * kBatchMaxGates]
     __shared__ int s_state;
     __shared__ double s_red[32];
     __shared__ HpsiTab tabs;
@@ -2991,7 +3061,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
             coef[2 * g] = (R)c;
             coef[2 * g + 1] = (R)sn;
         }
-        for (int j = threadIdx.x; j < nops * nwarps; j += NT) opacc[j] = 0.0;
+        for (int j = threadIdx.x; j < nops * nwarps; j += NT) opacc[j] = 0;
         for (size_t i = threadIdx.x; i < N; i += NT) psi[i] = mk<R>(i == a.init_index ? 1 : 0, 0);
         __syncthreads();
         // ---- QSU
@@ -3133,13 +3203,15 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                         }
                     }
                 }
+                R el = 0;
 #pragma unroll
                 for (int j = 0; j < EPT; ++j) {
                     const uint32_t e = threadIdx.x + j * NT;
                     if (e >= E) continue;
                     lam[rep ^ spanv[e >> C.kl] ^ (e & lm)] = acc[j];
-                    if (hp == a.nhpass - 1) eacc += (double)(cur[e].x * acc[j].x + cur[e].y * acc[j].y);
+                    el += cur[e].x * acc[j].x + cur[e].y * acc[j].y;
                 }
+                if (hp == a.nhpass - 1) eacc += (double)el;
                 __syncthreads();
             }
         }
@@ -3192,7 +3264,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                     R g = adjoint_op<R>(tp, tl, P.k, op, coef, nullptr);
                     if (has_param(op.kind)) {
                         g = warp_sum<R>(g);
-                        if (lane == 0) opacc[(o - o0) * nwarps + warp] += (double)g;
+                        if (lane == 0) opacc[(o - o0) * nwarps + warp] += g;
                     }
                     __syncthreads();
                 }
@@ -3212,7 +3284,7 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
                 const int p = a.gparam[g0 + op.gate];
                 if (p < 0 || !has_param(op.kind)) continue;
                 double v = 0.0;
-                for (int w = 0; w < nwarps; ++w) v += opacc[o * nwarps + w];
+                for (int w = 0; w < nwarps; ++w) v += (double)opacc[o * nwarps + w];
                 a.grads[p0 + p] += v;
             }
             a.t_start[st] = t0;
@@ -3363,8 +3435,8 @@ size_t adj_smem(sv_dtype dt, int k, int nlow, int nops, int threads) {
     return 2 * ((size_t)1 << k) * es + ((size_t)1 << (k - nlow)) * 8 + (size_t)nops * (threads / 32) * 8 + 64;
 }
 size_t coset_smem(sv_dtype dt, int E, int m, int nslots, int nwarps) {
-    const size_t es = dt == SV_C64 ? 8 : 16;
-    return 2 * (size_t)E * es + ((size_t)1 << m) * 8 + (size_t)nslots * nwarps * 8;
+    const size_t rb = dt == SV_C64 ? 4 : 8;
+    return evc_span_end((uint32_t)E, m, rb) + evc_slot_bytes(nslots, nwarps, rb);
 }
 
 }  // namespace
