@@ -2539,6 +2539,100 @@ __device__ __forceinline__ R evc_all2(uint32_t sb, const Cx<R> *own, uint32_t B,
     return val[0];
 }
 
+// complex64 forms of evc_sel2 / evc_all2 on packed f32x2 registers: the
+// products (v.x u.x, v.y u.y) -- or, with the partner's halves swapped on
+// load, (v.y u.x, v.x u.y) for the imaginary part -- and the level folds run
+// on both halves at once; the halves are combined at the end
+__device__ __forceinline__ unsigned long long lds_b64(uint32_t addr) {
+    unsigned long long v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ unsigned long long lds_b64_swap(uint32_t addr) {
+    float x, y;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(addr));
+    return f2_pack(y, x);
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+struct LevP { unsigned long long s[4]; };
+template <bool ODD> __device__ __forceinline__ float f2_combine(unsigned long long r) {
+    const float2 h = f2_unpack(r);
+    return ODD ? h.y - h.x : h.x + h.y;
+}
+template <int EPT, int H, int S, bool ODD>
+__device__ __forceinline__ float evc_sel2p(uint32_t sb, const unsigned long long *own, uint32_t B, const LevP &lv) {
+    constexpr int N = EPT / 2;
+    unsigned long long val[N];
+#pragma unroll
+    for (int jp = 0; jp < N; ++jp) {
+        const int j0 = ((jp >> H) << (H + 1)) | (jp & ((1 << H) - 1));
+        const uint32_t ad = sb + (B ^ ((uint32_t)j0 << 12));
+        val[jp] = f2_mul(ODD ? lds_b64_swap(ad) : lds_b64(ad), own[j0 | (S << H)]);
+    }
+#pragma unroll
+    for (int i = 0, n = N; n > 1; ++i, n >>= 1) {
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) val[k] = f2_fma(lv.s[i], val[2 * k + 1], val[2 * k]);
+    }
+    return f2_combine<ODD>(val[0]);
+}
+template <int EPT, bool ODD>
+__device__ __forceinline__ float evc_all2p(uint32_t sb, const unsigned long long *own, uint32_t B, bool diag,
+                                           const LevP &lv) {
+    unsigned long long val[EPT];
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        if (diag) {
+            val[j] = f2_mul(own[j], own[j]);
+        } else {
+            const uint32_t ad = sb + (B ^ ((uint32_t)j << 12));
+            val[j] = f2_mul(ODD ? lds_b64_swap(ad) : lds_b64(ad), own[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0, n = EPT; n > 1; ++i, n >>= 1) {
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) val[k] = f2_fma(lv.s[i], val[2 * k + 1], val[2 * k]);
+    }
+    return f2_combine<ODD>(val[0]);
+}
+
+// Coset copy of the ring's layout (E = 512 EPT, 16-byte chunks, 2^kl-element
+// runs with kl small enough that a thread's chunks share their position
+// inside a run): chunk i of thread t is element c = t P + 512 P i, P per
+// chunk; its span index (c >> kl) = c0 + i step and run offset c & lowmask
+// are per-thread constants, so each chunk costs one span load and an xor.
+struct RingLoad {
+    uint32_t s0, step;
+    uint64_t low;
+};
+template <typename R>
+__device__ __forceinline__ RingLoad ring_load_setup(int kl) {
+    constexpr uint32_t P = 16 / sizeof(Cx<R>);
+    const uint32_t c = threadIdx.x * P;
+    return {c >> kl, (512u * P) >> kl, (uint64_t)(c & ((1u << kl) - 1u))};
+}
+template <typename R, int EPT>
+__device__ __forceinline__ void ring_load(Cx<R> *dst, const Cx<R> *psi, uint64_t rep, const uint64_t *spanv,
+                                          const RingLoad &L) {
+    constexpr uint32_t P = 16 / sizeof(Cx<R>);
+    const uint64_t rc = rep ^ L.low;
+    const uint64_t *sp = spanv + L.s0;
+    Cx<R> *d = dst + threadIdx.x * P;
+#pragma unroll
+    for (int i = 0; i < EPT / (int)P; ++i) cp_async16(d + 512 * P * i, psi + (rc ^ sp[i * L.step]));
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ psi, const CosetArgs a,
                                                      const DevGroup *__restrict__ groups,
@@ -2551,6 +2645,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
     Cx<R> *buf = reinterpret_cast<Cx<R> *>(smem);
     uint64_t *spanv = reinterpret_cast<uint64_t *>(buf + 3 * (size_t)E);
     __shared__ LevT<R> glev[kEvcFew];
+    __shared__ LevP glevp[kEvcFew];                 // complex64: the level signs packed (s, s)
     __shared__ uint64_t gz[kEvcFew];
     __shared__ R gfac[kEvcFew];
     __shared__ double wsum[kEvcFew][NT / 32];
@@ -2589,6 +2684,10 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
 #pragma unroll
                 for (int i = 0; i < 4; ++i) lv.s[i] = ((wf >> i) & 1u) ? (R)-1 : (R)1;
                 glev[g] = lv;
+                if constexpr (sizeof(R) == 4) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) glevp[g].s[i] = f2_pack((float)lv.s[i], (float)lv.s[i]);
+                }
                 gz[g] = S.z;
                 gfac[g] = (R)ps.fac;
             }
@@ -2599,8 +2698,14 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
     const uint64_t mine = blockIdx.x < ncos ? (ncos - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
     uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
+    // per-thread copy constants when a thread's chunks share their run offset
+    const bool rl = a.kl <= 9 + (sizeof(R) == 4 ? 1 : 0);
+    const RingLoad RL = ring_load_setup<R>(rl ? a.kl : 0);
     for (uint64_t k = 0; k < 2; ++k) {
-        if (k < mine) load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
+        if (k < mine) {
+            if (rl) ring_load<R, EPT>(buf + k * E, psi, rep_pf, spanv, RL);
+            else load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
+        }
         cp_async_commit();
         rep_pf = walk_next(rep_pf, bw);
     }
@@ -2613,16 +2718,48 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
         cp_async_wait1();
         __syncthreads();
         // coset it + 2 into the buffer of coset it - 1 (every thread is past it)
-        if (it + 2 < mine) load_coset<R>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, a.kl, E);
+        if (it + 2 < mine) {
+            if (rl) ring_load<R, EPT>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, RL);
+            else load_coset<R>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, a.kl, E);
+        }
         cp_async_commit();
         rep_pf = walk_next(rep_pf, bw);
         const Cx<R> *t = buf + (it % 3) * E;
         const uint32_t sb = smem_u32(t);
+        const uint32_t bmask =
+            tmask ^ __ballot_sync(0xffffffffu, lane < ng && ((__popcll(rep & gz[lane < ng ? lane : 0]) & 1) != 0));
+        if constexpr (sizeof(R) == 4) {
+            unsigned long long own[EPT];
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) own[j] = lds_b64(sb + ((threadIdx.x + j * NT) << 3));
+#pragma unroll
+            for (int g = 0; g < kEvcFew; ++g) {
+                if (g < ng) {
+                    const uint32_t B = pk[g] & 0xFFFFFu, code = pk[g] >> 20;
+                    const LevP lv = glevp[g];
+                    float v;
+                    switch (code) {
+                    case 0: v = evc_all2p<EPT, false>(sb, own, B, false, lv); break;
+                    case 16: v = evc_all2p<EPT, true>(sb, own, B, false, lv); break;
+                    case 31: v = evc_all2p<EPT, false>(sb, own, B, true, lv); break;
+#define SV_SEL2P(HH, SS, OO)                                                                                 \
+    case (HH + 1) | (SS << 3) | (OO << 4):                                                                   \
+        if constexpr ((2 << HH) <= EPT) v = evc_sel2p<EPT, HH, SS, OO != 0>(sb, own, B, lv);                 \
+        else v = 0;                                                                                          \
+        break;
+#define SV_SEL2P_4(HH) SV_SEL2P(HH, 0, 0) SV_SEL2P(HH, 1, 0) SV_SEL2P(HH, 0, 1) SV_SEL2P(HH, 1, 1)
+                        SV_SEL2P_4(0) SV_SEL2P_4(1) SV_SEL2P_4(2) SV_SEL2P_4(3)
+#undef SV_SEL2P_4
+#undef SV_SEL2P
+                    default: v = 0; break;
+                    }
+                    acc[g] += ((bmask >> g) & 1u) ? -v : v;
+                }
+            }
+        } else {
         Cx<R> own[EPT];
 #pragma unroll
         for (int j = 0; j < EPT; ++j) own[j] = t[threadIdx.x + j * NT];
-        const uint32_t bmask =
-            tmask ^ __ballot_sync(0xffffffffu, lane < ng && ((__popcll(rep & gz[lane < ng ? lane : 0]) & 1) != 0));
 #pragma unroll
         for (int g = 0; g < kEvcFew; ++g) {
             if (g < ng) {
@@ -2646,6 +2783,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
                 }
                 acc[g] += ((bmask >> g) & 1u) ? -v : v;
             }
+        }
         }
         if ((it & 63) == 63 || it + 1 == mine) {
             // flush: FP64 warp sums (times the pair factor) into the per-warp slots (fixed order)
