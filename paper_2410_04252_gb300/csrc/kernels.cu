@@ -2497,9 +2497,8 @@ template <typename R> struct LevT { R s[4]; };
 
 // sum over the selected elements (bit H of j equal to S; j' = j with bit H
 // removed) of the pair term, folded by the level signs
-template <typename R, int EPT, int H, int S, bool ODD>
+template <typename R, int EPT, int SH, int H, int S, bool ODD>
 __device__ __forceinline__ R evc_sel2(uint32_t sb, const Cx<R> *own, uint32_t B, const LevT<R> &lv) {
-    constexpr int SH = 9 + (sizeof(R) == 4 ? 3 : 4);
     constexpr int N = EPT / 2;
     R val[N];
 #pragma unroll
@@ -2517,9 +2516,8 @@ __device__ __forceinline__ R evc_sel2(uint32_t sb, const Cx<R> *own, uint32_t B,
     return val[0];
 }
 // every element (no split; X = 0 gives |own|^2)
-template <typename R, int EPT, bool ODD>
+template <typename R, int EPT, int SH, bool ODD>
 __device__ __forceinline__ R evc_all2(uint32_t sb, const Cx<R> *own, uint32_t B, bool diag, const LevT<R> &lv) {
-    constexpr int SH = 9 + (sizeof(R) == 4 ? 3 : 4);
     R val[EPT];
 #pragma unroll
     for (int j = 0; j < EPT; ++j) {
@@ -2569,14 +2567,14 @@ template <bool ODD> __device__ __forceinline__ float f2_combine(unsigned long lo
     const float2 h = f2_unpack(r);
     return ODD ? h.y - h.x : h.x + h.y;
 }
-template <int EPT, int H, int S, bool ODD>
+template <int EPT, int SH, int H, int S, bool ODD>
 __device__ __forceinline__ float evc_sel2p(uint32_t sb, const unsigned long long *own, uint32_t B, const LevP &lv) {
     constexpr int N = EPT / 2;
     unsigned long long val[N];
 #pragma unroll
     for (int jp = 0; jp < N; ++jp) {
         const int j0 = ((jp >> H) << (H + 1)) | (jp & ((1 << H) - 1));
-        const uint32_t ad = sb + (B ^ ((uint32_t)j0 << 12));
+        const uint32_t ad = sb + (B ^ ((uint32_t)j0 << SH));
         val[jp] = f2_mul(ODD ? lds_b64_swap(ad) : lds_b64(ad), own[j0 | (S << H)]);
     }
 #pragma unroll
@@ -2586,7 +2584,7 @@ __device__ __forceinline__ float evc_sel2p(uint32_t sb, const unsigned long long
     }
     return f2_combine<ODD>(val[0]);
 }
-template <int EPT, bool ODD>
+template <int EPT, int SH, bool ODD>
 __device__ __forceinline__ float evc_all2p(uint32_t sb, const unsigned long long *own, uint32_t B, bool diag,
                                            const LevP &lv) {
     unsigned long long val[EPT];
@@ -2595,7 +2593,7 @@ __device__ __forceinline__ float evc_all2p(uint32_t sb, const unsigned long long
         if (diag) {
             val[j] = f2_mul(own[j], own[j]);
         } else {
-            const uint32_t ad = sb + (B ^ ((uint32_t)j << 12));
+            const uint32_t ad = sb + (B ^ ((uint32_t)j << SH));
             val[j] = f2_mul(ODD ? lds_b64_swap(ad) : lds_b64(ad), own[j]);
         }
     }
@@ -2607,22 +2605,22 @@ __device__ __forceinline__ float evc_all2p(uint32_t sb, const unsigned long long
     return f2_combine<ODD>(val[0]);
 }
 
-// Coset copy of the ring's layout (E = 512 EPT, 16-byte chunks, 2^kl-element
+// Coset copy of the ring's layout (E = NT EPT, 16-byte chunks, 2^kl-element
 // runs with kl small enough that a thread's chunks share their position
-// inside a run): chunk i of thread t is element c = t P + 512 P i, P per
+// inside a run): chunk i of thread t is element c = t P + NT P i, P per
 // chunk; its span index (c >> kl) = c0 + i step and run offset c & lowmask
 // are per-thread constants, so each chunk costs one span load and an xor.
 struct RingLoad {
     uint32_t s0, step;
     uint64_t low;
 };
-template <typename R>
+template <typename R, int NT>
 __device__ __forceinline__ RingLoad ring_load_setup(int kl) {
     constexpr uint32_t P = 16 / sizeof(Cx<R>);
     const uint32_t c = threadIdx.x * P;
-    return {c >> kl, (512u * P) >> kl, (uint64_t)(c & ((1u << kl) - 1u))};
+    return {c >> kl, ((uint32_t)NT * P) >> kl, (uint64_t)(c & ((1u << kl) - 1u))};
 }
-template <typename R, int EPT>
+template <typename R, int EPT, int NT>
 __device__ __forceinline__ void ring_load(Cx<R> *dst, const Cx<R> *psi, uint64_t rep, const uint64_t *spanv,
                                           const RingLoad &L) {
     constexpr uint32_t P = 16 / sizeof(Cx<R>);
@@ -2630,15 +2628,16 @@ __device__ __forceinline__ void ring_load(Cx<R> *dst, const Cx<R> *psi, uint64_t
     const uint64_t *sp = spanv + L.s0;
     Cx<R> *d = dst + threadIdx.x * P;
 #pragma unroll
-    for (int i = 0; i < EPT / (int)P; ++i) cp_async16(d + 512 * P * i, psi + (rc ^ sp[i * L.step]));
+    for (int i = 0; i < EPT / (int)P; ++i) cp_async16(d + NT * P * i, psi + (rc ^ sp[i * L.step]));
 }
 
-template <typename R, int EPT>
-__global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ psi, const CosetArgs a,
-                                                     const DevGroup *__restrict__ groups,
-                                                     const DevString *__restrict__ strs, double *__restrict__ part,
-                                                     int part_stride) {
-    constexpr int NT = 512;
+template <typename R, int EPT, int LOGNT>
+__global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_ring(const Cx<R> *__restrict__ psi, const CosetArgs a,
+                                                            const DevGroup *__restrict__ groups,
+                                                            const DevString *__restrict__ strs,
+                                                            double *__restrict__ part, int part_stride) {
+    constexpr int NT = 1 << LOGNT;
+    constexpr int SH = LOGNT + (sizeof(R) == 4 ? 3 : 4);   // byte offset of element row j: j << SH
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t E = 1u << (a.kl + a.m);
     const int ng = a.g_end - a.g_begin;          // == number of strings (one per group), at most kEvcFew
@@ -2672,7 +2671,6 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
             const uint32_t neg0 = G.X ? (uint32_t)((S.nY == 1) | (S.nY == 2)) : 0u;
             const uint32_t tconst = ((uint32_t)__popc(tc.l & (uint32_t)S.z) ^ (uint32_t)__popc(tc.a0 & S.bz) ^ neg0 ^
                                      flip) & 1u;
-            constexpr int SH = 9 + (sizeof(R) == 4 ? 3 : 4);
             uint32_t B = (threadIdx.x ^ G.X) * (uint32_t)sizeof(Cx<R>);
             if (ps.h >= 0) B ^= (uint32_t)ps.s << (ps.h + SH);
             const uint32_t code = G.X ? ((uint32_t)(ps.h + 1) | ((uint32_t)ps.s << 3) | ((uint32_t)(S.nY & 1) << 4))
@@ -2699,11 +2697,11 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
     const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
     uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
     // per-thread copy constants when a thread's chunks share their run offset
-    const bool rl = a.kl <= 9 + (sizeof(R) == 4 ? 1 : 0);
-    const RingLoad RL = ring_load_setup<R>(rl ? a.kl : 0);
+    const bool rl = a.kl <= LOGNT + (sizeof(R) == 4 ? 1 : 0);
+    const RingLoad RL = ring_load_setup<R, NT>(rl ? a.kl : 0);
     for (uint64_t k = 0; k < 2; ++k) {
         if (k < mine) {
-            if (rl) ring_load<R, EPT>(buf + k * E, psi, rep_pf, spanv, RL);
+            if (rl) ring_load<R, EPT, NT>(buf + k * E, psi, rep_pf, spanv, RL);
             else load_coset<R>(buf + k * E, psi, rep_pf, spanv, a.kl, E);
         }
         cp_async_commit();
@@ -2719,7 +2717,7 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
         __syncthreads();
         // coset it + 2 into the buffer of coset it - 1 (every thread is past it)
         if (it + 2 < mine) {
-            if (rl) ring_load<R, EPT>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, RL);
+            if (rl) ring_load<R, EPT, NT>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, RL);
             else load_coset<R>(buf + ((it + 2) % 3) * E, psi, rep_pf, spanv, a.kl, E);
         }
         cp_async_commit();
@@ -2739,12 +2737,12 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
                     const LevP lv = glevp[g];
                     float v;
                     switch (code) {
-                    case 0: v = evc_all2p<EPT, false>(sb, own, B, false, lv); break;
-                    case 16: v = evc_all2p<EPT, true>(sb, own, B, false, lv); break;
-                    case 31: v = evc_all2p<EPT, false>(sb, own, B, true, lv); break;
+                    case 0: v = evc_all2p<EPT, SH, false>(sb, own, B, false, lv); break;
+                    case 16: v = evc_all2p<EPT, SH, true>(sb, own, B, false, lv); break;
+                    case 31: v = evc_all2p<EPT, SH, false>(sb, own, B, true, lv); break;
 #define SV_SEL2P(HH, SS, OO)                                                                                 \
     case (HH + 1) | (SS << 3) | (OO << 4):                                                                   \
-        if constexpr ((2 << HH) <= EPT) v = evc_sel2p<EPT, HH, SS, OO != 0>(sb, own, B, lv);                 \
+        if constexpr ((2 << HH) <= EPT) v = evc_sel2p<EPT, SH, HH, SS, OO != 0>(sb, own, B, lv);             \
         else v = 0;                                                                                          \
         break;
 #define SV_SEL2P_4(HH) SV_SEL2P(HH, 0, 0) SV_SEL2P(HH, 1, 0) SV_SEL2P(HH, 0, 1) SV_SEL2P(HH, 1, 1)
@@ -2767,12 +2765,12 @@ __global__ void __launch_bounds__(512, 1) k_evc_ring(const Cx<R> *__restrict__ p
                 const LevT<R> lv = glev[g];
                 R v;
                 switch (code) {
-                case 0: v = evc_all2<R, EPT, false>(sb, own, B, false, lv); break;
-                case 16: v = evc_all2<R, EPT, true>(sb, own, B, false, lv); break;
-                case 31: v = evc_all2<R, EPT, false>(sb, own, B, true, lv); break;
+                case 0: v = evc_all2<R, EPT, SH, false>(sb, own, B, false, lv); break;
+                case 16: v = evc_all2<R, EPT, SH, true>(sb, own, B, false, lv); break;
+                case 31: v = evc_all2<R, EPT, SH, false>(sb, own, B, true, lv); break;
 #define SV_SEL2(HH, SS, OO)                                                                                  \
     case (HH + 1) | (SS << 3) | (OO << 4):                                                                   \
-        if constexpr ((2 << HH) <= EPT) v = evc_sel2<R, EPT, HH, SS, OO != 0>(sb, own, B, lv);               \
+        if constexpr ((2 << HH) <= EPT) v = evc_sel2<R, EPT, SH, HH, SS, OO != 0>(sb, own, B, lv);           \
         else v = 0;                                                                                          \
         break;
 #define SV_SEL2_4(HH) SV_SEL2(HH, 0, 0) SV_SEL2(HH, 1, 0) SV_SEL2(HH, 0, 1) SV_SEL2(HH, 1, 1)
@@ -3821,13 +3819,13 @@ cudaError_t evc_dispatch(cudaStream_t st, int grid, const void *psi, const Coset
     // threads: a multiple of the run length, at least one warp, at most 512
     const int threads = std::max(std::max(32, 1 << a.kl), std::min(E, 512));
     const int ept = std::max(1, E / threads);
-    if (a.few && threads == 512 && ept >= 2 && ept <= 16 && E == (uint32_t)ept * 512u &&
-        3 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8 + 4096 <= (size_t)smem_optin()) {
+    const bool ring_fits = 3 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8 + 4096 <= (size_t)smem_optin();
+    if (a.few && threads == 512 && ept >= 2 && ept <= 16 && E == (uint32_t)ept * 512u && ring_fits) {
         const size_t smr = 3 * (size_t)E * sizeof(Cx<R>) + ((size_t)1 << a.m) * 8;
 #define SV_EVCR_CASE(N)                                                                                      \
     case N:                                                                                                  \
-        allow_smem(k_evc_ring<R, N>, smr);                                                                   \
-        k_evc_ring<R, N><<<grid, 512, smr, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride);    \
+        allow_smem(k_evc_ring<R, N, 9>, smr);                                                                \
+        k_evc_ring<R, N, 9><<<grid, 512, smr, st>>>((const Cx<R> *)psi, a, groups, strs, part, part_stride); \
         return cudaGetLastError();
         switch (ept) {
             SV_EVCR_CASE(2)
