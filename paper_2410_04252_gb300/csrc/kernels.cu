@@ -2697,7 +2697,8 @@ __global__ void __launch_bounds__(1 << LOGNT, 1) k_evc_ring(const Cx<R> *__restr
     const BitWalk bw = bit_walk(a.freeb, a.nfree, gridDim.x);
     uint64_t rep_pf = deposit(blockIdx.x, a.freeb, a.nfree), rep_cur = rep_pf;
     // per-thread copy constants when a thread's chunks share their run offset
-    const bool rl = a.kl <= LOGNT + (sizeof(R) == 4 ? 1 : 0);
+    const bool rl = a.kl <= LOGNT + (sizeof(R) == 4 ? 1 : 0) && (16u >> a.kl) <= (uint32_t)sizeof(Cx<R>) &&
+                    (EPT * sizeof(Cx<R>)) % 16 == 0;
     const RingLoad RL = ring_load_setup<R, NT>(rl ? a.kl : 0);
     for (uint64_t k = 0; k < 2; ++k) {
         if (k < mine) {
