@@ -137,9 +137,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind: str, launches_bytes: float):
-    """Per-launch DRAM bytes of `kind` from the committed ncu summary, or None
-    if absent or taken on different kernel sources."""
+def ncu_traffic(workload: str, kind: str):
+    """Per-launch DRAM bytes of `kind` in `workload` from the committed ncu
+    summary, or None if absent or taken on different kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
@@ -147,7 +147,7 @@ def ncu_traffic(kind: str, launches_bytes: float):
         d = json.load(f)
     if d.get("source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kind)
+    k = d.get("workloads", {}).get(workload, {}).get(kind)
     if not k:
         return None
     return k.get("dram_bytes_per_full_launch")
@@ -412,7 +412,7 @@ def measure(wl, schedule, steps, warmup, clocks=None):
     return out
 
 
-def kernel_table(agg, steps, peak, peak_src):
+def kernel_table(agg, steps, peak, peak_src, workload=""):
     """Per-kind summary and the dominant kind's roofline entry."""
     kinds = {}
     total = max(sum(v[2] for v in agg.values()), 1e-9)
@@ -426,7 +426,7 @@ def kernel_table(agg, steps, peak, peak_src):
     cnt, byts, ms = agg[dom]
     achieved = byts / (ms * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dom, byts / cnt)}
+            "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(workload, dom)}
     return kinds, roof
 
 
@@ -452,7 +452,8 @@ def extra_workload(cfg_id, steps, warmup, peak, peak_src, local, dtype=None, eag
     wl = Workload(cfg_id, dtype=dtype)
     try:
         m = measure(wl, sv.LAZY, steps, warmup, ClockSampler(local))
-        kinds, roof = kernel_table(m["agg"], steps, peak, peak_src)
+        kinds, roof = kernel_table(m["agg"], steps, peak, peak_src,
+                                   wl.cfg["name"] if dtype is None else wl.cfg["name"].replace("c64", "c128"))
         h2d, d2h = wl.bytes_io()
         state_gb = (1 << wl.n) * (8 if wl.dtype == sv.C64 else 16) / 1e9
         d = {"workload": wl.cfg["name"] if dtype is None else wl.cfg["name"].replace("c64", "c128"),
@@ -565,7 +566,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    kinds, roof = kernel_table(m["agg"], args.steps, peak, peak_src)
+    kinds, roof = kernel_table(m["agg"], args.steps, peak, peak_src, cfg["name"] if n == cfg["n"] else "")
     cpu = None
     if not args.no_cpu:
         n_s = min(args.cpu_n, n)
@@ -690,7 +691,8 @@ def run_batch(args, emit=True):
                    "tile_bits": opt.tile_bits, "threads": opt.threads, "fuse_max": opt.fuse_max,
                    "autotuned": tuned_ms is not None},
         "roofline": {"bound": "hbm", "kernel": "batch", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_src, "traffic": None},
+                     "frac": achieved / peak, "peak_source": peak_src,
+                     "traffic": ncu_traffic(cfg["name"], "batch") if n == cfg["n"] else None},
         "cpu_baseline": cpu,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                        "max": lat[-1]},
