@@ -221,6 +221,19 @@ def oracle_step(cfg_id, n_s):
     return ms, what
 
 
+def workload_config(cfg_id, n, world):
+    """The workload's identity as both arms print it in `config` (host data
+    only: no library call)."""
+    from paper_2410_04252_gb300 import workloads as W
+    cfg = W.CONFIGS[cfg_id]
+    circ = W.make_circuit(cfg, n)
+    state_gb = (1 << n) * (8 if cfg["dtype"] == "c64" else 16) / 1e9
+    return {"workload": cfg["name"], "n": n, "g": cfg["g"], "layers": cfg["layers"], "gates": circ.m,
+            "params": circ.nparams, "nterms": cfg["nterms"], "schedule": "lazy", "state_GB": state_gb,
+            "l2": "inputs larger than L2 (state %.1f GB)" % state_gb,
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands, timed for real on the
     host cores, each step one run of the workload's QSU + EVC at --ref-n
@@ -249,11 +262,11 @@ def run_reference(args):
     if cfg["work"] == "batch":
         metric = BATCH_METRIC
         value, unit, hib = 1.0 / (ms * 1e-3), "states/s", True
+    config = workload_config(args.config, n_full, world) if cfg["work"] != "batch" else {"workload": cfg["name"]}
     line = {"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg["name"], "n": n_s, "n_workload": n_full, "g": cfg["g"],
-                       "nterms": cfg["nterms"], "sample": what},
+            "config": config, "sample": {"n": n_s, "what": what},
             "cpu_baseline": {"value": value, "unit": unit, "cores": omp_threads(), "kind": "oracle",
                              "sample": what + " (measured, median of the timed steps)"},
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -591,12 +604,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 (f32 math, f64 accumulation)" if dtype == sv.C64 else "c128 (f64)",
         "data": "synthetic",
-        "config": {"workload": cfg["name"], "n": n, "g": g, "layers": cfg["layers"], "gates": circ.m,
-                   "params": circ.nparams, "nterms": len(coeffs), "schedule": "lazy",
-                   "state_GB": state_gb, "l2": "inputs larger than L2 (state %.1f GB)" % state_gb,
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "tile_bits": opt.tile_bits, "low_bits": opt.low_bits, "evc_low_bits": opt.evc_low_bits,
-                   "evc_span": opt.evc_span},
+        "config": workload_config(args.config, n, world),
+        "options": {"tile_bits": opt.tile_bits, "low_bits": opt.low_bits, "evc_low_bits": opt.evc_low_bits,
+                    "evc_span": opt.evc_span},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
