@@ -155,6 +155,8 @@ void sv_destroy(sv_handle *h);
  * torch tensor's data_ptr).  The library never frees it.  bytes must be
  * >= 2^n * sizeof(amplitude); the pointer must be 256-byte aligned. */
 sv_status sv_attach_state(sv_handle *h, void *dev_ptr, size_t bytes);
+/* The same call under the name of the original interface sketch. */
+sv_status sv_attach_buffer(sv_handle *h, void *dev_ptr, size_t bytes);
 /* Attach a caller-owned device buffer for the adjoint vector lambda = H psi
  * (same size and alignment rules).  Without it sv_grad allocates one. */
 sv_status sv_attach_lambda(sv_handle *h, void *dev_ptr, size_t bytes);

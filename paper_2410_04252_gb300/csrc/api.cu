@@ -841,6 +841,8 @@ sv_status sv_attach_state(sv_handle *h, void *p, size_t bytes) {
     return SV_OK;
 }
 
+sv_status sv_attach_buffer(sv_handle *h, void *p, size_t bytes) { return sv_attach_state(h, p, bytes); }
+
 sv_status sv_attach_lambda(sv_handle *h, void *p, size_t bytes) {
     SV_TRY(check_handle(h));
     if (!p || bytes < h->state_bytes()) return fail(SV_EINVAL, "lambda buffer too small");

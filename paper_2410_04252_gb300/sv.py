@@ -84,6 +84,7 @@ EXPORTS = {
     "sv_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_H)]),
     "sv_destroy": (None, [_H]),
     "sv_attach_state": (ctypes.c_int, [_H, _vp, _sz]),
+    "sv_attach_buffer": (ctypes.c_int, [_H, _vp, _sz]),
     "sv_attach_lambda": (ctypes.c_int, [_H, _vp, _sz]),
     "sv_set_stream": (ctypes.c_int, [_H, _vp]),
     "sv_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
