@@ -1508,10 +1508,28 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
         }
         {
             Cx<R> *tpc = reinterpret_cast<Cx<R> *>(tp), *tlc = reinterpret_cast<Cx<R> *>(tl);
-            for (uint32_t j = threadIdx.x; j < T; j += NT) {
-                const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
-                tpc[swz_tile(j)] = psi[gi];
-                tlc[swz_tile(j)] = lam[gi];
+            if (T == (uint32_t)(V * NT)) {
+                // every load of the thread in flight before the first store
+                Cx<R> vp[V], vl[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t j = threadIdx.x + (uint32_t)v * NT;
+                    const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
+                    vp[v] = psi[gi];
+                    vl[v] = lam[gi];
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t j = threadIdx.x + (uint32_t)v * NT;
+                    tpc[swz_tile(j)] = vp[v];
+                    tlc[swz_tile(j)] = vl[v];
+                }
+            } else {
+                for (uint32_t j = threadIdx.x; j < T; j += NT) {
+                    const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
+                    tpc[swz_tile(j)] = psi[gi];
+                    tlc[swz_tile(j)] = lam[gi];
+                }
             }
         }
         __syncthreads();
