@@ -3142,6 +3142,28 @@ __device__ __noinline__ void batch_reg_forward(Cx<R> *tile, const GatePassArgs &
     }
 }
 
+// psi and lambda tiles of a register-phased reverse pass staged swizzled,
+// with all of a thread's V loads of both in flight before its first store
+template <typename R, int V>
+__device__ __noinline__ void batch_load_pair(Cx<R> *tp, Cx<R> *tl, const Cx<R> *psi, const Cx<R> *lam, uint64_t base,
+                                             const uint64_t *hioff, int nlow) {
+    const uint32_t lowmask = (1u << nlow) - 1u;
+    Cx<R> vp[V], vl[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const uint32_t j = threadIdx.x + (uint32_t)v * blockDim.x;
+        const uint64_t gi = base | hioff[j >> nlow] | (j & lowmask);
+        vp[v] = psi[gi];
+        vl[v] = lam[gi];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const uint32_t j = threadIdx.x + (uint32_t)v * blockDim.x;
+        tp[swz_tile(j)] = vp[v];
+        tl[swz_tile(j)] = vl[v];
+    }
+}
+
 template <typename R, int RB>
 __device__ __noinline__ void batch_reg_adjoint(Cx<R> *tp, Cx<R> *tl, const GatePassArgs &P, const DevOp *ops,
                                   const Phase *phases, const R *coef, R *opacc, int o0) {
@@ -3391,11 +3413,10 @@ __global__ void __launch_bounds__(512, 1) k_batch(const BatchArgs a) {
             for (uint64_t ti = 0; ti < (1ull << P.nout); ++ti) {
                 const uint64_t base = deposit(ti, P.out, P.nout);
                 if (rb >= 2 && rb <= 4) {
-                    for (uint32_t j = threadIdx.x; j < T; j += NT) {
-                        const uint64_t gi = base | hioff[j >> P.nlow] | (j & lowmask);
-                        tp[swz_tile(j)] = psi[gi];
-                        tl[swz_tile(j)] = lam[gi];
-                    }
+                    // T = 2^rb x 512 here
+                    if (rb == 4) batch_load_pair<R, 16>(tp, tl, psi, lam, base, hioff, P.nlow);
+                    else if (rb == 3) batch_load_pair<R, 8>(tp, tl, psi, lam, base, hioff, P.nlow);
+                    else batch_load_pair<R, 4>(tp, tl, psi, lam, base, hioff, P.nlow);
                     __syncthreads();
                     if (rb == 4) batch_reg_adjoint<R, 4>(tp, tl, P, a.ops, a.phases, coef, opacc, o0);
                     else if (rb == 3) batch_reg_adjoint<R, 3>(tp, tl, P, a.ops, a.phases, coef, opacc, o0);
