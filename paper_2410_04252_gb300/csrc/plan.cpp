@@ -475,6 +475,14 @@ uint32_t phase_lanes(uint32_t rmask, int k) {
         lanes |= 1u << t;
         ++nl;
     }
+    // the fifth lane bit (the half-warp bit) above the four independent ones,
+    // so that lanes 0-15 of a warp hit 16 distinct slots mod 16
+    const int top = lanes ? 31 - __builtin_clz(lanes) : -1;
+    for (int t = top + 1; t < k && nl < 5; ++t)
+        if (!(rmask >> t & 1u) && !(lanes >> t & 1u)) {
+            lanes |= 1u << t;
+            ++nl;
+        }
     for (int t = 0; t < k && nl < 5; ++t)
         if (!(rmask >> t & 1u) && !(lanes >> t & 1u)) {
             lanes |= 1u << t;
