@@ -3132,6 +3132,7 @@ __device__ __noinline__ void batch_reg_forward(Cx<R> *tile, const GatePassArgs &
         const Phase F = phases[ph];
         uint32_t base, sp[V];
         phase_index<RB>(F.rmask, P.k, base, sp);
+        base = phase_base(F.rmask, F.lanes, P.k);   // the phase's lane bits (conflict-free half-warps)
         Cx<R> x[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) x[v] = tile[swz_tile(base | sp[v])];
@@ -3173,6 +3174,7 @@ __device__ __noinline__ void batch_reg_adjoint(Cx<R> *tp, Cx<R> *tl, const GateP
         const Phase F = phases[ph];
         uint32_t base, sp[V];
         phase_index<RB>(F.rmask, P.k, base, sp);
+        base = phase_base(F.rmask, F.lanes, P.k);   // the phase's lane bits (conflict-free half-warps)
         Cx<R> xp[V], xl[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
