@@ -1253,7 +1253,7 @@ __host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, 
     L.prb = o;   o = align16u(o + 8u * nph);
     // adjoint gradient slots: per op and warp a partial of the state's real
     // type, and for complex64 an FP64 total per op (flushed every kAdjFlush tiles)
-    L.acc = o;   o = align16u(o + (adj ? ((uint32_t)amp / 2u) * (kRegThreads / 32) * nops : 0u));
+    L.acc = o;   o = align16u(o + (adj ? ((uint32_t)amp / 2u) * kAdjSlotStride * nops : 0u));
     L.tot = o;   o = align16u(o + (adj && amp == 8 ? 8u * nops : 0u));
     L.area = o;  o = align16u(o + (uint32_t)a.area);
     L.total = o;
@@ -1470,13 +1470,16 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
     const uint32_t T = 1u << a.k;
     const int nops = a.op_end - a.op_begin;
     const int NT = blockDim.x, nwarps = NT >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // slot row stride nwarps + 1: the lanes 0, 8, 16, 24 that add the four
+    // gradients of a step (ops o .. o+3) hit four different banks
+    const int AS = kAdjSlotStride;
     RA<R> *tl = reinterpret_cast<RA<R> *>(smem);           // lambda tile, then the psi tile
     RA<R> *tp = tl + T;
     unsigned char *sm = smem + 2 * T * sizeof(RA<R>);
     const RegLayout L = reg_layout(a, (int)sizeof(Cx<R>), true);
     R *acc = reinterpret_cast<R *>(sm + L.acc);
     double *tot64 = reinterpret_cast<double *>(sm + L.tot);
-    for (int j = threadIdx.x; j < nops * nwarps; j += NT) acc[j] = 0;
+    for (int j = threadIdx.x; j < nops * AS; j += NT) acc[j] = 0;
     if constexpr (sizeof(R) == 4)
         for (int j = threadIdx.x; j < nops; j += NT) tot64[j] = 0.0;
     reg_setup<R, RB>(sm, L, a, ops, phases, steps, coef, dblocks, dmem, true);
@@ -1566,7 +1569,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
 #pragma unroll
                     for (int b = 0; b < RB; ++b) {
                         if (!((S.a >> b) & 1)) continue;
-                        if (lane == 8 * b) acc[o * nwarps + warp] += tot;
+                        if (lane == 8 * b) acc[o * AS + warp] += tot;
                         ++o;
                         const Cx<R> k = *c++;
                         const RotK<R> rk = rotk<R>(k.x, k.y);
@@ -1595,7 +1598,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                         for (int mi = B.m_begin; mi < B.m_end; ++mi) {
                             const DiagMember m = mem[mi - a.mem_begin];
                             if (m.type == SV_DM_REG_RZ && lane == 8 * m.a)
-                                acc[(m.op - a.op_begin) * nwarps + warp] += red;
+                                acc[(m.op - a.op_begin) * AS + warp] += red;
                         }
                     } else {
                         // thread RZ members: +-tot by the thread's bit, four at a time
@@ -1615,7 +1618,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                             const R red = warp_sum4<R>(vals[0], vals[1], vals[2], vals[3]);
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
-                                if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * nwarps + warp] += red;
+                                if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * AS + warp] += red;
                         }
                     }
                     reg_diag<R, RB>(xp, B, area);
@@ -1626,7 +1629,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     R g = ra_adjoint_op<R, RB>(xp, xl, op, P.rmask, base, cs[S.a - a.op_begin], mats);
                     if (has_param(op.kind)) {
                         g = warp_sum<R>(g);
-                        if (lane == 0) acc[(S.a - a.op_begin) * nwarps + warp] += g;
+                        if (lane == 0) acc[(S.a - a.op_begin) * AS + warp] += g;
                     }
                 }
             }
@@ -1654,8 +1657,8 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                 for (int o = threadIdx.x; o < nops; o += NT) {
                     float f = 0.f;
                     for (int w = 0; w < nwarps; ++w) {
-                        f += acc[o * nwarps + w];
-                        acc[o * nwarps + w] = 0.f;
+                        f += acc[o * AS + w];
+                        acc[o * AS + w] = 0.f;
                     }
                     tot64[o] += (double)f;
                 }
@@ -1667,7 +1670,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
         double tsum = 0.0;
         if constexpr (sizeof(R) == 4) tsum = tot64[o];
         else
-            for (int w = 0; w < nwarps; ++w) tsum += acc[o * nwarps + w];
+            for (int w = 0; w < nwarps; ++w) tsum += acc[o * AS + w];
         part[(size_t)blockIdx.x * part_stride + a.op_begin + o] = tsum;
     }
 }

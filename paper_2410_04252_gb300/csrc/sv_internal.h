@@ -120,6 +120,7 @@ SV_HD inline uint32_t swz_slot(uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8)) &
 // the tiles, tables and accumulators, and each block takes
 // diag_block_bytes() of it.
 constexpr int kRegSmemLimit = 226 * 1024;
+constexpr int kAdjSlotStride = kRegThreads / 32 + 1;   // adjoint gradient slots per op (one per warp, padded)
 inline int diag_block_bytes(int kind, int k, int amp) {
     const int V = 1 << (k - 9);
     return kind == 0 ? V * V * amp + 512 : 512 * amp;
@@ -129,7 +130,7 @@ inline int reg_pass_fixed_bytes(int k, int nlow, int nops, int nsteps, int nphas
     // steps, block headers, per-phase thread bases and register offsets,
     // FP64 per-warp gradient slots, alignment
     return 2 * (1 << k) * amp + 8 * (1 << (k - nlow)) + nops * amp + 16 * nsteps + 32 * kMaxPassDiag +
-           16 * nops + nphases * (2 * kRegThreads + 8) + nops * (kRegThreads / 32) * 8 + 256;
+           16 * nops + nphases * (2 * kRegThreads + 8) + nops * kAdjSlotStride * 8 + 256;
 }
 struct RegStep {
     int32_t type, a;
