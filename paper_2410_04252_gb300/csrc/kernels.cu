@@ -908,6 +908,75 @@ __device__ __forceinline__ void ra_rot(RA<R> *x, const RotK<R> &k) {
     }
 }
 
+// RY with its larger coefficient factored out (the factor is common to every
+// amplitude of the tile, so a pass carries the product of the factors and
+// applies it once when the tile is stored):
+//   |c| >= |s|: RY = c [[1, -t], [t, 1]], t = s / c   (form A)
+//   |c| <  |s|: RY = s [[t, -1], [1, t]], t = c / s   (form B)
+// so |t| <= 1, the factor is at least 1/sqrt(2) in magnitude, and a pair
+// costs two fused multiply-adds (form B: plus a sign flip) instead of two
+// products and two fused multiply-adds.
+template <typename R> struct RotF;
+template <> struct RotF<float> { unsigned long long T, NT; };
+template <> struct RotF<double> { double t; };
+template <typename R> __device__ __forceinline__ RotF<R> rotf(R t);
+template <> __device__ __forceinline__ RotF<float> rotf<float>(float t) { return {f2_pack(t, t), f2_pack(-t, -t)}; }
+template <> __device__ __forceinline__ RotF<double> rotf<double>(double t) { return {t}; }
+
+// factored form (t, factor) and form bit of an RY with coefficients (c, s)
+template <typename R> __device__ __forceinline__ Cx<R> ry_factored(R c, R s, int &form_b) {
+    const bool b = fabs(s) > fabs(c);
+    form_b = b ? 1 : 0;
+    return b ? mk<R>(c / s, s) : mk<R>(s / c, c);
+}
+
+template <typename R, int V, int B, bool FB>
+__device__ __forceinline__ void ra_rotf(RA<R> *x, const RotF<R> &k) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        if (v & (1 << B)) continue;
+        const int w = v | (1 << B);
+        if constexpr (sizeof(R) == 4) {
+            unsigned long long uu, vv;
+            if (FB) {   // (t u - v, u + t v)
+                const unsigned long long nw = x[w] ^ 0x8000000080000000ull;
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(x[v]), "l"(k.T), "l"(nw));
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(x[w]), "l"(k.T), "l"(x[v]));
+            } else {    // (u - t v, v + t u)
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(uu) : "l"(x[w]), "l"(k.NT), "l"(x[v]));
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(vv) : "l"(x[v]), "l"(k.T), "l"(x[w]));
+            }
+            x[v] = uu;
+            x[w] = vv;
+        } else {
+            const double2 a = x[v], b = x[w];
+            if (FB) {
+                x[v] = make_double2(fma(k.t, a.x, -b.x), fma(k.t, a.y, -b.y));
+                x[w] = make_double2(fma(k.t, b.x, a.x), fma(k.t, b.y, a.y));
+            } else {
+                x[v] = make_double2(fma(-k.t, b.x, a.x), fma(-k.t, b.y, a.y));
+                x[w] = make_double2(fma(k.t, a.x, b.x), fma(k.t, a.y, b.y));
+            }
+        }
+    }
+}
+
+// one factored RY on register bit b (0..RB-1) in form fb
+template <typename R, int V, int RB>
+__device__ __forceinline__ void ra_rotf_bit(RA<R> *x, int b, bool fb, const RotF<R> &k) {
+    switch (b * 2 + (fb ? 1 : 0)) {
+    case 0: ra_rotf<R, V, 0, false>(x, k); break;
+    case 1: ra_rotf<R, V, 0, true>(x, k); break;
+    case 2: if constexpr (RB > 1) ra_rotf<R, V, 1, false>(x, k); break;
+    case 3: if constexpr (RB > 1) ra_rotf<R, V, 1, true>(x, k); break;
+    case 4: if constexpr (RB > 2) ra_rotf<R, V, 2, false>(x, k); break;
+    case 5: if constexpr (RB > 2) ra_rotf<R, V, 2, true>(x, k); break;
+    case 6: if constexpr (RB > 3) ra_rotf<R, V, 3, false>(x, k); break;
+    case 7: if constexpr (RB > 3) ra_rotf<R, V, 3, true>(x, k); break;
+    default: break;
+    }
+}
+
 // Gradient part of an RY on register bit B: sum over pairs (v, w = v | bit B)
 // of Re(conj(l_w) p_v) - Re(conj(l_v) p_w)  (= Im<lambda|Y|psi> on the pairs).
 template <typename R, int V, int B>
@@ -1233,7 +1302,7 @@ __device__ __forceinline__ void load_tile_async(E *tile, const Cx<R> *psi, uint6
 // Shared-memory layout of a register-blocked pass (both kernels): the tiles,
 // then these tables (offsets in bytes from the end of the tiles).
 struct RegLayout {
-    uint32_t hioff, cs, steps, blocks, mem, pbase, prb, acc, tot, area, total;
+    uint32_t hioff, cs, steps, blocks, mem, pbase, prb, acc, tot, sc, area, total;
 };
 // FP64 is 1/64 of the FP32 rate on this part: per-tile gradient partials stay
 // in FP32 slots and reach FP64 once every kAdjFlush tiles
@@ -1255,6 +1324,9 @@ __host__ __device__ inline RegLayout reg_layout(const GatePassArgs &a, int amp, 
     // type, and for complex64 an FP64 total per op (flushed every kAdjFlush tiles)
     L.acc = o;   o = align16u(o + (adj ? ((uint32_t)amp / 2u) * kAdjSlotStride * nops : 0u));
     L.tot = o;   o = align16u(o + (adj && amp == 8 ? 8u * nops : 0u));
+    // factored RYs: per step the product of the factors applied before it
+    // (adjoint), and the pass's total factor (entry nst)
+    L.sc = o;    o = align16u(o + ((uint32_t)amp / 2u) * (nst + 1u));
     L.area = o;  o = align16u(o + (uint32_t)a.area);
     L.total = o;
     return L;
@@ -1283,7 +1355,44 @@ __device__ void reg_setup(unsigned char *sm, const RegLayout &L, const GatePassA
         const int gi = ops[o].gate;
         cs[o - a.op_begin] = mk<R>(coef[2 * gi], adj ? -coef[2 * gi + 1] : coef[2 * gi + 1]);
     }
-    for (int s = a.st_begin + tid; s < a.st_end; s += NT) st[s - a.st_begin] = steps[s];
+    __syncthreads();
+    // the RYs of ROT steps as (t, factor), each step carrying their forms
+    // (bit 8 + register bit set: form B)
+    for (int s = a.st_begin + tid; s < a.st_end; s += NT) {
+        RegStep S = steps[s];
+        if (S.type == SV_STEP_ROT) {
+            int o = S.op_begin;
+            for (int b = 0; b < RB; ++b) {
+                if (!((S.a >> b) & 1)) continue;
+                const Cx<R> k = cs[o - a.op_begin];
+                int fb;
+                cs[o - a.op_begin] = ry_factored<R>(k.x, k.y, fb);
+                if (fb) S.a |= 1 << (8 + b);
+                ++o;
+            }
+        }
+        st[s - a.st_begin] = S;
+    }
+    // prefix products of the factors in execution order (forward: ascending
+    // steps; adjoint: descending), entry nst = the pass's total factor
+    if (tid == 0) {
+        R *sc = reinterpret_cast<R *>(sm + L.sc);
+        const int nst = a.st_end - a.st_begin;
+        R f = 1;
+        for (int i = 0; i < nst; ++i) {
+            const int s = adj ? a.st_end - 1 - i : a.st_begin + i;
+            sc[s - a.st_begin] = f;
+            const RegStep S = steps[s];
+            if (S.type != SV_STEP_ROT) continue;
+            for (int o = S.op_begin; o < S.op_end; ++o) {
+                const int gi = ops[o].gate;
+                const R c = coef[2 * gi], sn = adj ? -coef[2 * gi + 1] : coef[2 * gi + 1];
+                int fb;
+                f *= ry_factored<R>(c, sn, fb).y;
+            }
+        }
+        sc[nst] = f;
+    }
     for (int b = a.db_begin + tid; b < a.db_end; b += NT) bl[b - a.db_begin] = dblocks[b];
     DiagMember *mem = reinterpret_cast<DiagMember *>(sm + L.mem);
     for (int m = a.mem_begin + tid; m < a.mem_end; m += NT) mem[m - a.mem_begin] = dmem[m];
@@ -1386,6 +1495,7 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
     const RegLayout L = reg_layout(a, (int)sizeof(Cx<R>), false);
     reg_setup<R, RB>(sm, L, a, ops, phases, steps, coef, dblocks, dmem, false);
     __syncthreads();
+    const R ftot = reinterpret_cast<const R *>(sm + L.sc)[a.st_end - a.st_begin];   // product of the RY factors
     const uint64_t *hioff = reinterpret_cast<const uint64_t *>(sm + L.hioff);
     const Cx<R> *cs = reinterpret_cast<const Cx<R> *>(sm + L.cs);
     const RegStep *st = reinterpret_cast<const RegStep *>(sm + L.steps);
@@ -1422,19 +1532,13 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
             for (int s = P.st_begin; s < P.st_end; ++s) {
                 const RegStep S = st[s - a.st_begin];
                 if (S.type == SV_STEP_ROT) {
+                    // factored RYs (t, factor): the factors are applied at the store
                     const Cx<R> *c = cs + (S.op_begin - a.op_begin);
 #pragma unroll
                     for (int b = 0; b < RB; ++b) {
                         if (!((S.a >> b) & 1)) continue;
                         const Cx<R> k = *c++;
-                        const RotK<R> rk = rotk<R>(k.x, k.y);
-                        switch (b) {
-                        case 0: ra_rot<R, V, 0>(x, rk); break;
-                        case 1: if constexpr (RB > 1) ra_rot<R, V, 1>(x, rk); break;
-                        case 2: if constexpr (RB > 2) ra_rot<R, V, 2>(x, rk); break;
-                        case 3: if constexpr (RB > 3) ra_rot<R, V, 3>(x, rk); break;
-                        default: break;
-                        }
+                        ra_rotf_bit<R, V, RB>(x, b, (S.a >> (8 + b)) & 1, rotf<R>(k.x));
                     }
                 } else if (S.type == SV_STEP_DIAG) {
                     reg_diag<R, RB>(x, bl[S.a - a.db_begin], area);
@@ -1449,7 +1553,10 @@ __global__ void __launch_bounds__(512, 1) k_gate_reg(Cx<R> *__restrict__ psi, co
             __syncthreads();
         }
         const Cx<R> *tc = reinterpret_cast<const Cx<R> *>(tile);
-        for (uint32_t j = threadIdx.x; j < T; j += NT) psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = tc[swz_tile(j)];
+        for (uint32_t j = threadIdx.x; j < T; j += NT) {
+            const Cx<R> v = tc[swz_tile(j)];
+            psi[gbase | hioff[j >> a.nlow] | (j & lowmask)] = mk<R>(v.x * ftot, v.y * ftot);
+        }
         __syncthreads();
         if (it + 2 < mine) load_tile_async<R>(tile, psi, base_pf, hioff, a.nlow, T);
         cp_async_commit();
@@ -1484,6 +1591,11 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
         for (int j = threadIdx.x; j < nops; j += NT) tot64[j] = 0.0;
     reg_setup<R, RB>(sm, L, a, ops, phases, steps, coef, dblocks, dmem, true);
     __syncthreads();
+    // factored RYs: before step s both registers sets hold the true vectors
+    // divided by scf[s], so a gradient part computed there is scaled by
+    // scf[s]^2; the stores multiply by the total factor
+    const R *scf = reinterpret_cast<const R *>(sm + L.sc);
+    const R ftot = scf[a.st_end - a.st_begin];
     const uint64_t *hioff = reinterpret_cast<const uint64_t *>(sm + L.hioff);
     const Cx<R> *cs = reinterpret_cast<const Cx<R> *>(sm + L.cs);
     const RegStep *st = reinterpret_cast<const RegStep *>(sm + L.steps);
@@ -1549,6 +1661,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
             }
             for (int s = P.st_end - 1; s >= P.st_begin; --s) {
                 const RegStep S = st[s - a.st_begin];
+                const R fs = scf[s - a.st_begin], fs2 = fs * fs;
                 if (S.type == SV_STEP_ROT) {
                     // every RY of the step: gradient part at the step's end (they commute), then RY^dagger
                     R g[4] = {0, 0, 0, 0};
@@ -1563,7 +1676,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                         default: break;
                         }
                     }
-                    const R tot = warp_sum4<R>(g[0], g[1], g[2], g[3]);
+                    const R tot = warp_sum4<R>(g[0], g[1], g[2], g[3]) * fs2;
                     const Cx<R> *c = cs + (S.op_begin - a.op_begin);
                     int o = S.op_begin - a.op_begin;
 #pragma unroll
@@ -1572,14 +1685,10 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                         if (lane == 8 * b) acc[o * AS + warp] += tot;
                         ++o;
                         const Cx<R> k = *c++;
-                        const RotK<R> rk = rotk<R>(k.x, k.y);
-                        switch (b) {
-                        case 0: ra_rot<R, V, 0>(xp, rk); ra_rot<R, V, 0>(xl, rk); break;
-                        case 1: if constexpr (RB > 1) { ra_rot<R, V, 1>(xp, rk); ra_rot<R, V, 1>(xl, rk); } break;
-                        case 2: if constexpr (RB > 2) { ra_rot<R, V, 2>(xp, rk); ra_rot<R, V, 2>(xl, rk); } break;
-                        case 3: if constexpr (RB > 3) { ra_rot<R, V, 3>(xp, rk); ra_rot<R, V, 3>(xl, rk); } break;
-                        default: break;
-                        }
+                        const RotF<R> rk = rotf<R>(k.x);
+                        const bool fb = (S.a >> (8 + b)) & 1;
+                        ra_rotf_bit<R, V, RB>(xp, b, fb, rk);
+                        ra_rotf_bit<R, V, RB>(xl, b, fb, rk);
                     }
                 } else if (S.type == SV_STEP_DIAG) {
                     // every RZ member's generator expectation at the block's end (Z
@@ -1594,7 +1703,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     if (B.kind == 0) {
                         R sb[4] = {0, 0, 0, 0};
                         signed_bit_sums<R, RB>(tv, sb);
-                        const R red = warp_sum4<R>(sb[0], sb[1], sb[2], sb[3]);
+                        const R red = warp_sum4<R>(sb[0], sb[1], sb[2], sb[3]) * fs2;
                         for (int mi = B.m_begin; mi < B.m_end; ++mi) {
                             const DiagMember m = mem[mi - a.mem_begin];
                             if (m.type == SV_DM_REG_RZ && lane == 8 * m.a)
@@ -1615,7 +1724,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                                     }
                                 }
                             }
-                            const R red = warp_sum4<R>(vals[0], vals[1], vals[2], vals[3]);
+                            const R red = warp_sum4<R>(vals[0], vals[1], vals[2], vals[3]) * fs2;
 #pragma unroll
                             for (int j = 0; j < 4; ++j)
                                 if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * AS + warp] += red;
@@ -1628,7 +1737,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                     if (has_out_target(op)) op = resolve_out(op, gbase);
                     R g = ra_adjoint_op<R, RB>(xp, xl, op, P.rmask, base, cs[S.a - a.op_begin], mats);
                     if (has_param(op.kind)) {
-                        g = warp_sum<R>(g);
+                        g = warp_sum<R>(g) * fs2;
                         if (lane == 0) acc[(S.a - a.op_begin) * AS + warp] += g;
                     }
                 }
@@ -1646,8 +1755,9 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
             const Cx<R> *tpc = reinterpret_cast<const Cx<R> *>(tp), *tlc = reinterpret_cast<const Cx<R> *>(tl);
             for (uint32_t j = threadIdx.x; j < T; j += NT) {
                 const uint64_t gi = gbase | hioff[j >> a.nlow] | (j & lowmask);
-                psi[gi] = tpc[swz_tile(j)];
-                lam[gi] = tlc[swz_tile(j)];
+                const Cx<R> p = tpc[swz_tile(j)], l = tlc[swz_tile(j)];
+                psi[gi] = mk<R>(p.x * ftot, p.y * ftot);
+                lam[gi] = mk<R>(l.x * ftot, l.y * ftot);
             }
         }
         __syncthreads();

@@ -128,9 +128,9 @@ inline int diag_block_bytes(int kind, int k, int amp) {
 inline int reg_pass_fixed_bytes(int k, int nlow, int nops, int nsteps, int nphases, int amp) {
     // adjoint (the larger): psi and lambda tiles, high offsets, (c, s) per op,
     // steps, block headers, per-phase thread bases and register offsets,
-    // FP64 per-warp gradient slots, alignment
+    // per-warp gradient slots, the RY factor per step, alignment
     return 2 * (1 << k) * amp + 8 * (1 << (k - nlow)) + nops * amp + 16 * nsteps + 32 * kMaxPassDiag +
-           16 * nops + nphases * (2 * kRegThreads + 8) + nops * kAdjSlotStride * 8 + 256;
+           16 * nops + nphases * (2 * kRegThreads + 8) + nops * kAdjSlotStride * 8 + 8 * (nsteps + 1) + 272;
 }
 struct RegStep {
     int32_t type, a;
