@@ -1471,6 +1471,31 @@ __device__ __forceinline__ void reg_diag(RA<R> *x, const DiagBlock &B, const uns
     }
 }
 
+// The same diagonal on two register sets (the adjoint's psi and lambda),
+// each table entry loaded once.
+template <typename R, int RB>
+__device__ __forceinline__ void reg_diag2(RA<R> *x, RA<R> *y, const DiagBlock &B, const unsigned char *area) {
+    constexpr int V = 1 << RB;
+    if (B.kind == 0) {
+        const Cx<R> *tab = reinterpret_cast<const Cx<R> *>(area + B.smem);
+        const uint32_t zm = area[B.smem + V * V * (int)sizeof(Cx<R>) + threadIdx.x];
+        const Cx<R> *col = tab + zm;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const Cx<R> w = col[v * V];
+            x[v] = ra_cmul<R>(x[v], w);
+            y[v] = ra_cmul<R>(y[v], w);
+        }
+    } else {
+        const Cx<R> w = reinterpret_cast<const Cx<R> *>(area + B.smem)[threadIdx.x];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            x[v] = ra_cmul<R>(x[v], w);
+            y[v] = ra_cmul<R>(y[v], w);
+        }
+    }
+}
+
 // The thread's 2^RB shared-memory indices of a phase (swizzled; the swizzle
 // is linear, so index(base | sp[v]) = swz(base) ^ XOR of swz(register bits)).
 template <int RB>
@@ -1730,8 +1755,7 @@ __global__ void __launch_bounds__(512, 1) k_adj_reg(Cx<R> *__restrict__ psi, Cx<
                                 if (lane == 8 * j && opi[j] >= 0) acc[opi[j] * AS + warp] += red;
                         }
                     }
-                    reg_diag<R, RB>(xp, B, area);
-                    reg_diag<R, RB>(xl, B, area);
+                    reg_diag2<R, RB>(xp, xl, B, area);
                 } else {
                     DevOp op = ops[S.a];
                     if (has_out_target(op)) op = resolve_out(op, gbase);
