@@ -458,7 +458,7 @@ def other_schedule(wl, schedule, steps, warmup, ref):
 
 
 def extra_workload(cfg_id, steps, warmup, peak, peak_src, local, dtype=None, eager=True):
-    """A further workload of the benchmark (a BASELINE config) on this GPU:
+    """A further workload of the benchmark on this GPU:
     its own timed region, clocks, roofline of its dominant kernel, end-to-end
     time and, for QSU / EVC workloads, the eager schedule beside it."""
     from paper_2410_04252_gb300 import sv
