@@ -53,3 +53,24 @@ def test_reduce_times_single_rank():
     dev, wall, per_step, iters_per_s, e2e = bench.reduce_times(90.0, 120.0, 3, 1)
     assert (dev, wall, per_step, e2e) == (90.0, 120.0, 30.0, 40.0)
     assert iters_per_s == pytest.approx(3 / 0.09)
+
+
+def test_reference_arm_line():
+    """The reference arm (the oracle as it stands, on the host cores) prints
+    one JSON line under the GPU arm's workload config, with a timed value,
+    its sample and the e2e / cpu_baseline keys of the contract."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                          "--ref-n", "10"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([ln for ln in out.stdout.splitlines() if ln.startswith("{")][-1])
+    import bench
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.workload_config(3, 32, 1)
+    assert line["sample"]["n"] == 10 and line["value"] > 0 and line["ms_per_step"] == line["value"]
+    assert line["higher_is_better"] is False and line["unit"] == "ms" and line["steps"] == 2
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
