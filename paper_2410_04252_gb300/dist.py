@@ -186,16 +186,19 @@ def _physical(mask: int, l2p) -> int:
     return out
 
 
-def sharded_energy(n: int, circ, params, ham, chunk, init_index: int = 0, group=None):
+def sharded_energy(n: int, circ, params, ham, chunk, init_index: int = 0, group=None, schedule=None,
+                   options=None):
     """E = sum_t a_t <psi|P_t|psi> with psi = U|init> on the state sharded
     over the ranks of `group` (a power of two, 2^g ranks: global qubits = the
-    top g physical bits).  QSU follows the library's lazy plan (Alg. 1-3):
-    before each tile its QR (qr_exchange), then the tile's gates on every
-    chunk; EVC follows the lazy EVC plan (Alg. 6, diagonalized targets) from
-    the final QSU layout: per tile its QR, then every string's local sum,
-    signed by the chunk's global bits under its Z letters; the per-string
-    values are summed over the ranks.  `chunk` (2^L amplitudes) is
-    overwritten.  Returns (energy, per-string values, final layout)."""
+    top g physical bits).  QSU follows the library's plan under `schedule`
+    (default the lazy plan, Alg. 1-3; the hierarchical plan, Alg. 4/5, with
+    options.intra_bits global qubits inside a node): before each tile its QR
+    (qr_exchange), then the tile's gates on every chunk; EVC follows the lazy
+    EVC plan (Alg. 6, diagonalized targets) from the final QSU layout: per
+    tile its QR, then every string's local sum, signed by the chunk's global
+    bits under its Z letters; the per-string values are summed over the
+    ranks.  `chunk` (2^L amplitudes) is overwritten.  Returns (energy,
+    per-string values, final layout)."""
     import torch.distributed as dist
     from . import sv
     world = dist.get_world_size(group)
@@ -209,7 +212,7 @@ def sharded_energy(n: int, circ, params, ham, chunk, init_index: int = 0, group=
     chunk.zero_()
     if init_index >> L == rank:
         chunk[init_index & ((1 << L) - 1)] = 1
-    plan = sv.plan_qsu(n, g, circ, sv.LAZY)
+    plan = sv.plan_qsu(n, g, circ, sv.LAZY if schedule is None else schedule, options)
     l2p = list(range(n))
     for t in plan["tiles"]:
         qr_exchange(chunk, L, rank, t["pairs"], group)

@@ -104,7 +104,7 @@ def _letters(x, z, n):
     return out
 
 
-def _energy_rank(rank, world, port, q, n, layers, nterms):
+def _energy_rank(rank, world, port, q, n, layers, nterms, intra_bits=0):
     dist = _init(rank, world, port)
     try:
         import oracle
@@ -129,7 +129,13 @@ def _energy_rank(rank, world, port, q, n, layers, nterms):
         ham = _narrow_hamiltonian(n, nterms, n - (world.bit_length() - 1))
         L = n - (world.bit_length() - 1)
         chunk = torch.zeros(1 << L, dtype=torch.complex128)
-        e, vals, l2p = D.sharded_energy(n, circ, params, ham, chunk)
+        if intra_bits:
+            from paper_2410_04252_gb300 import sv
+            o = sv.default_options()
+            o.intra_bits = intra_bits
+            e, vals, l2p = D.sharded_energy(n, circ, params, ham, chunk, schedule=sv.HIER, options=o)
+        else:
+            e, vals, l2p = D.sharded_energy(n, circ, params, ham, chunk)
         q.put((rank, e, vals, l2p, chunk.numpy().copy()))
     finally:
         dist.destroy_process_group()
@@ -143,13 +149,15 @@ def _narrow_hamiltonian(n, nterms, nL):
     return W.Hamiltonian(n, h.letters[keep].copy(), h.coeffs[keep].copy())
 
 
-@pytest.mark.parametrize("world", [2, 4])
-def test_sharded_energy_matches_single_buffer(world):
+@pytest.mark.parametrize("world,intra_bits", [(2, 0), (4, 0), (4, 1)])
+def test_sharded_energy_matches_single_buffer(world, intra_bits):
+    """Lazy plan on 2 and 4 ranks; hierarchical plan (Alg. 4/5) on 4 ranks
+    with one global qubit inside a node."""
     import oracle
     from paper_2410_04252_gb300 import sv
     from paper_2410_04252_gb300 import workloads as W
     n, layers, nterms = 8, 3, 40
-    got = _run(world, _energy_rank, (n, layers, nterms))
+    got = _run(world, _energy_rank, (n, layers, nterms, intra_bits))
     energies = [v[1] for v in got]
     assert max(energies) == min(energies)            # every rank holds the reduced result
     e, vals, l2p = got[0][1], got[0][2], got[0][3]
@@ -158,8 +166,14 @@ def test_sharded_energy_matches_single_buffer(world):
     params = W.uniform_params(circ.nparams, 31, 0.0, 2 * np.pi)
     ham = _narrow_hamiltonian(n, nterms, n - (world.bit_length() - 1))
     # single buffer, the plan's gate order, then the final layout's permutation
-    plan = sv.plan_qsu(n, world.bit_length() - 1, circ, sv.LAZY)
+    if intra_bits:
+        o = sv.default_options()
+        o.intra_bits = intra_bits
+        plan = sv.plan_qsu(n, world.bit_length() - 1, circ, sv.HIER, o)
+    else:
+        plan = sv.plan_qsu(n, world.bit_length() - 1, circ, sv.LAZY)
     order = plan["order"]
+    assert any(t["pairs"] for t in plan["tiles"])           # the exchange ran
     c = W.Circuit(n, circ.kinds[order], circ.qubits[order], circ.param[order], circ.mat[order], circ.nparams)
     psi = oracle.apply_circuit(oracle.basis_state(n, 0), c, params)
     phys = np.empty_like(psi)
