@@ -1864,6 +1864,11 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
     const uint32_t runmask = (1u << a.L) - 1u;
     const uint64_t ntiles = 1ull << a.nout;
     const bool vec = (VEC == 2) && a.L >= 1;
+    // no in-tile exchange moves bit 0: the source slots of a 16-byte pair are
+    // adjacent (the swizzle keeps bit 0), so the pair is one 16-byte load
+    bool bit0_fixed = true;
+    for (int i = 0; i < a.nlo; ++i)
+        if (a.la[i] == 0 || a.lb[i] == 0) bit0_fixed = false;
     const BitWalk bw = bit_walk(a.out, a.nout, gridDim.x);
     uint64_t bnext = deposit(blockIdx.x, a.out, a.nout);
     for (uint64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
@@ -1892,7 +1897,16 @@ __global__ void __launch_bounds__(256) k_bitswap(Cx<R> *__restrict__ psi, const 
             }
         }
         __syncthreads();
-        if (vec) {
+        if (vec && bit0_fixed) {
+            for (uint32_t j = 2 * threadIdx.x; j < T; j += 2 * blockDim.x) {
+                const uint64_t off = hioff[j >> a.L] | (j & runmask);
+                const uint32_t s0 = pt[j >> 1] & 0xFFFFu;
+                const Cx<R> *src = self ? A : B;
+                *reinterpret_cast<float4 *>(&psi[b0 | off]) = *reinterpret_cast<const float4 *>(&src[s0]);
+                if (!self)
+                    *reinterpret_cast<float4 *>(&psi[b1 | off]) = *reinterpret_cast<const float4 *>(&A[s0]);
+            }
+        } else if (vec) {
             for (uint32_t j = 2 * threadIdx.x; j < T; j += 2 * blockDim.x) {
                 const uint64_t off = hioff[j >> a.L] | (j & runmask);
                 const uint32_t pp = pt[j >> 1], s0 = pp & 0xFFFFu, s1 = pp >> 16;
