@@ -207,3 +207,28 @@ def test_comm_cost_of_fig9():
     assert w == pytest.approx(0.75 * (1 << 25) * 16 / 100e9)
     flat = sv.plan_qsu(n, n - nL, c, sv.LAZY)
     assert D.qr_kinds(flat, n) == ["inter"] * 3     # no intra set: every QR crosses nodes
+
+
+def test_qr_exchange_rejects_pairs_that_are_not_local_global():
+    """A QR pair must be (local bit < L, global bit >= L); anything else is
+    refused before any data moves."""
+    from paper_2410_04252_gb300 import dist as D
+    chunk = torch.zeros(1 << 4, dtype=torch.complex128)
+    for pairs in ([(4, 5)], [(1, 3)], [(-1, 5)]):
+        with pytest.raises(ValueError):
+            D.qr_exchange(chunk, 4, 0, pairs)
+    D.qr_exchange(chunk, 4, 0, [])           # no pairs: nothing to do
+
+
+def test_comm_cost_counts_only_qrs():
+    """A plan without QRs costs nothing; weights scale the two QR kinds."""
+    from paper_2410_04252_gb300 import dist as D
+    plan = {"tiles": [{"local_mask": 0xFF, "pairs": []}]}
+    assert D.qr_kinds(plan, 10) == [] and D.comm_cost(plan, 10, 1.0, 5.0) == 0.0
+    plan = {"tiles": [{"local_mask": 0xFF, "pairs": []},
+                      {"local_mask": 0x1FE, "pairs": [(0, 8)], "intra_mask": 0x200},
+                      {"local_mask": 0x3FC, "pairs": [(1, 9)], "intra_mask": 0x002}]}
+    # the first QR changes the inter set {8, 9} -> {0}; the second swaps a
+    # local qubit with the intra one and leaves the inter set {0} alone
+    assert D.qr_kinds(plan, 10) == ["inter", "intra"]
+    assert D.comm_cost(plan, 10, 2.0, 7.0) == 9.0
